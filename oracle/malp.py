@@ -1,0 +1,164 @@
+"""Adaptive LP decoding (oracle): MALP-A (Algorithm 3), MALP-B and ALP
+(Algorithm 1).
+
+MALP-A (Section III-A):
+  1. The first LP holds only the one-sided box constraints of Eq. 8; its
+     solution u^0 is the bitwise hard decision (u_i = 0 if gamma_i >= 0,
+     else 1).
+  2. Repeat: for every check j with no ACTIVE parity inequality in the
+     current LP, run Algorithm 2 at u^{k-1}; if it finds a violated
+     inequality, drop j's old (inactive) inequality, if any, and add the new
+     one. If anything was added, solve the LP to get u^k. Stop when nothing
+     was added; u^k is the LP decoding solution.
+  MALP-B moves the removal to the start of the round: every inactive
+  inequality is dropped before the search. ALP never removes anything and
+  searches every check.
+
+An inequality is active when its slack x_{n+j} is zero (Section III-A). Each
+LP is solved by ``ipm.solve`` on the augmented form of ``lp.build``; the
+decisions are then taken on the optimal vertex recovered from the final
+iterate (``vertex.recover``), where a nonbasic slack is exactly zero, so
+"zero" is read as <= tau_act.
+
+Outputs (Section II-B, ML certificate): the solution u, the certificate flag
+(u is integral: max |u_i - round(u_i)| <= tau_int) and a hard decision. The
+decoder declares failure on a fractional u and the paper defines no hard
+decision for it; the oracle returns hard_i = [u_i > 1/2], except that an
+entry within tau_int of 1/2 takes the channel's hard decision (so a 1/2 entry
+does not turn on rounding noise).
+"""
+
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import cuts as _cuts
+from . import ipm as _ipm
+from . import lp as _lp
+from . import vertex as _vertex
+from .params import OracleParams, OK, NOT_CONVERGED
+
+
+@dataclasses.dataclass
+class LPRecord:
+    p: int
+    objective: float          # gamma'u^k
+    ipm_iters: int
+    u: np.ndarray
+    in_lp: np.ndarray
+    masks: np.ndarray
+    slack: np.ndarray          # slack per LP row
+    rows: np.ndarray
+
+
+@dataclasses.dataclass
+class DecodeResult:
+    u: np.ndarray              # float64 [n]
+    hard: np.ndarray           # uint8 [n]
+    cert: int                  # 1 = integral (ML codeword), 0 = fractional
+    in_lp: np.ndarray          # bool [m] final cut set
+    masks: np.ndarray          # uint32 [m] (0 where not in the LP)
+    alp_iters: int             # number of LPs solved
+    ipm_iters_total: int
+    lp_rows_final: int
+    objective: float           # gamma'u
+    status: int
+    history: list              # LPRecord per LP solved
+    cuts: list                 # final cut list (ALP keeps several per check)
+    vertex_failures: int = 0   # LPs whose vertex recovery was rejected
+
+
+def hard_decision(gamma: np.ndarray) -> np.ndarray:
+    """u^0 of Eq. 8: 0 where gamma_i >= 0, 1 where gamma_i < 0."""
+    return np.where(np.asarray(gamma) >= 0, 0.0, 1.0)
+
+
+def outputs(u: np.ndarray, gamma: np.ndarray, tau_int: float):
+    dist = np.abs(u - np.round(u))
+    cert = int(np.max(dist) <= tau_int) if u.size else 1
+    hard = (u > 0.5).astype(np.uint8)
+    near_half = np.abs(u - 0.5) <= tau_int
+    hard[near_half] = hard_decision(gamma)[near_half].astype(np.uint8)
+    return hard, cert
+
+
+def decode(code, gamma, params: OracleParams | None = None,
+           solve_normal_factory=None) -> DecodeResult:
+    """Decode one frame. ``solve_normal_factory(A)`` may replace the dense
+    Cholesky Newton solve (e.g. by PCG) for experiments."""
+    prm = params or OracleParams()
+    gamma = np.asarray(gamma, dtype=np.float64)
+    n, m = code.n, code.m
+    u = hard_decision(gamma)
+    in_lp = np.zeros(m, dtype=bool)
+    masks = np.zeros(m, dtype=np.uint32)
+    slack = np.full(m, np.inf)         # slack of check j's inequality
+    alp_cuts = []                      # ALP: ordered cut list
+    history = []
+    status = OK
+    ipm_total = 0
+    lps = 0
+    vfail = 0
+    while True:
+        flag = False
+        if prm.variant == "malp_b":
+            drop = in_lp & (slack > prm.tau_act)
+            in_lp[drop] = False
+            masks[drop] = 0
+        for j in range(m):
+            if prm.variant != "alp" and in_lp[j] and slack[j] <= prm.tau_act:
+                continue                # j has an active inequality
+            mask, lhs, violated = _cuts.find_violated(u[code.row(j)], prm.tau_cut)
+            if violated:
+                flag = True
+                if prm.variant == "alp":
+                    alp_cuts.append((j, mask))
+                    in_lp[j] = True
+                else:
+                    in_lp[j] = True     # replaces j's old inequality, if any
+                    masks[j] = mask
+        if not flag:
+            break
+        if lps >= prm.max_alp:
+            status = NOT_CONVERGED
+            break
+        if prm.variant == "alp":
+            lp = _lp.build_from_cuts(code, gamma, alp_cuts)
+        else:
+            lp = _lp.build(code, gamma, in_lp, masks)
+        solver = solve_normal_factory(lp.A) if solve_normal_factory else None
+        res = _ipm.solve(lp.A, lp.b, lp.c, prm, solve_normal=solver)
+        lps += 1
+        ipm_total += res.iters
+        xv, vok = _vertex.recover(lp.A, lp.b, lp.c, res.x, res.z)
+        vfail += int(not vok)
+        u = lp.u_from_x(xv)
+        s_rows = xv[n:]
+        slack = np.full(m, np.inf)
+        if prm.variant == "alp":
+            # several inequalities per check: a check counts as active if
+            # any of its inequalities is active
+            for r, j in enumerate(lp.rows):
+                slack[j] = min(slack[j], s_rows[r])
+        else:
+            slack[lp.rows] = s_rows
+        history.append(LPRecord(p=lp.p, objective=float(np.dot(gamma, u)),
+                                ipm_iters=res.iters, u=u.copy(),
+                                in_lp=in_lp.copy(), masks=masks.copy(),
+                                slack=s_rows.copy(), rows=lp.rows.copy()))
+        if res.status != OK:
+            status = NOT_CONVERGED
+            break
+    hard, cert = outputs(u, gamma, prm.tau_int)
+    out_masks = np.where(in_lp, masks, 0).astype(np.uint32)
+    final_cuts = alp_cuts if prm.variant == "alp" else \
+        [(int(j), int(masks[j])) for j in np.flatnonzero(in_lp)]
+    return DecodeResult(u=u, hard=hard, cert=cert, in_lp=in_lp.copy(),
+                        masks=out_masks, alp_iters=lps,
+                        ipm_iters_total=ipm_total,
+                        lp_rows_final=len(final_cuts),
+                        objective=float(np.dot(gamma, u)), status=status,
+                        history=history, cuts=final_cuts,
+                        vertex_failures=vfail)

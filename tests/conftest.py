@@ -1,0 +1,19 @@
+"""Shared test configuration.
+
+Tests marked ``gpu`` need a CUDA device and the compiled decoder library;
+everything else runs on the CPU (oracle pins, host logic, library symbols).
+"""
+
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled library")
+    config.addinivalue_line("markers", "slow: long-running CPU test")

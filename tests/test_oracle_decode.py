@@ -1,0 +1,170 @@
+"""Pins for the oracle decoder (MALP-A with the interior-point LP solver):
+the full LP decoding definition (Eq. 7, via a library simplex), exhaustive
+ML decoding (Eq. 3), the worked example of Remark 1, the invariants of
+Theorems 2-4 and Corollaries 3-5, and codeword symmetry.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import feldman, ipm, lp, vertex
+from oracle.params import OracleParams
+from synth import awgn_llr_frames, gallager_regular, named_code, random_codeword
+from synth.codes import from_dense
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_codes():
+    return [gallager_regular(n, 3, 6, seed=s, remove_4cycles=False) for n, s in
+            [(12, 1), (18, 2), (24, 3), (30, 4), (36, 5)]]
+
+
+@pytest.mark.parametrize("variant", ["malp_a", "malp_b", "alp"])
+def test_adaptive_equals_full_lp(variant):
+    """Theorem 2(c): ALP, MALP-A and MALP-B end at the LP decoding
+    solution of Eq. 7 (all parity inequalities + box)."""
+    prm = OracleParams(variant=variant)
+    for code in small_codes():
+        G = awgn_llr_frames(code.n, code.design_rate, 1.0, 11, range(6))
+        for g in G:
+            res = oracle.decode(code, g, prm)
+            u_ref, f_ref = feldman.lp_decode(code, g)
+            assert res.status == 0
+            assert abs(res.objective - f_ref) <= 1e-9 * (1 + abs(f_ref))
+            assert np.max(np.abs(res.u - u_ref)) < 1e-7
+
+
+def test_ml_certificate_property():
+    """Section II-B: an integral LP output is the ML codeword (exhaustive
+    ML over ker H, k <= 20)."""
+    seen_int = 0
+    for code in small_codes()[:4]:
+        G = awgn_llr_frames(code.n, code.design_rate, 2.0, 5, range(10))
+        for g in G:
+            res = oracle.decode(code, g)
+            if res.cert:
+                seen_int += 1
+                cw, cost = feldman.ml_decode(code, g)
+                assert np.array_equal(res.hard, cw)
+                assert abs(cost - res.objective) < 1e-9 * (1 + abs(cost))
+    assert seen_int > 10
+
+
+def test_hamming74_pseudocodeword():
+    """Remark 1: [1, 1/2, 0, 1/2, 0, 0, 1/2] is a pseudocodeword of the
+    (7,4,3) code with m = 3 fractional entries (fixture:
+    tests/golden/hamming74_pseudocodeword.json)."""
+    g = json.load(open(os.path.join(GOLDEN, "hamming74_pseudocodeword.json")))
+    code = from_dense(np.array(g["H"]))
+    res = oracle.decode(code, np.array(g["gamma"], dtype=float))
+    assert np.max(np.abs(res.u - np.array(g["u_expected"]))) < 1e-9
+    assert res.cert == g["cert_expected"]
+    assert int(np.sum(np.abs(res.u - np.round(res.u)) > 1e-6)) == code.m
+
+
+def _peel(H, E):
+    """Peeling (BEC) decoder on erased set E: True iff E has no stopping
+    set (Section III-C)."""
+    E = set(int(i) for i in E)
+    while E:
+        progress = False
+        for j in range(H.shape[0]):
+            nb = [i for i in np.flatnonzero(H[j]) if i in E]
+            if len(nb) == 1:
+                E.discard(nb[0])
+                progress = True
+        if not progress:
+            return False
+    return True
+
+
+def test_invariants_on_gallager_120():
+    code = named_code("gallager_120")
+    H = code.dense()
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(40))
+    n_int = 0
+    for g in G:
+        res = oracle.decode(code, g)
+        assert res.status == 0 and res.vertex_failures == 0
+        hard0 = (g < 0).astype(float)
+        objs = [h.objective for h in res.history]
+        # Theorem 2(b): strictly increasing cost, starting above gamma'u^0
+        assert all(b > a for a, b in zip([g @ hard0] + objs, objs))
+        # Theorem 2(c): at most n iterations
+        assert res.alp_iters <= code.n
+        for h in res.history:
+            # Theorem 2(a): box holds at every intermediate solution
+            assert h.u.min() >= -1e-9 and h.u.max() <= 1 + 1e-9
+            # Theorem 3 / Corollary 3: one inequality per check, p <= m
+            assert h.p == int(h.in_lp.sum()) <= code.m
+        # Corollary 5: at most m fractional entries
+        frac = np.abs(res.u - np.round(res.u)) > 1e-6
+        assert frac.sum() <= code.m
+        # the vertex differs from the hard decision only where the final
+        # LP's parity inequalities act (at most p_final positions)
+        assert np.sum(np.abs(res.u - hard0) > 1e-9) <= res.lp_rows_final
+        if res.cert:
+            n_int += 1
+            assert np.all((H.astype(int) @ res.hard) % 2 == 0)
+            # Theorem 4: the positions that changed contain no stopping set
+            assert _peel(H, np.flatnonzero(res.hard != hard0))
+    assert n_int > 20
+
+
+def test_codeword_symmetry():
+    """Sending codeword c instead of 0 maps gamma to gamma * (1 - 2c); the
+    polytope is symmetric under u -> |c - u| (the all-zero assumption of
+    Section III-C), so the whole adaptive run maps over."""
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(8))
+    for f, g in enumerate(G):
+        c = random_codeword(code, f)
+        g2 = g * (1.0 - 2.0 * c)
+        a = oracle.decode(code, g)
+        b = oracle.decode(code, g2)
+        assert np.max(np.abs(b.u - np.abs(c - a.u))) < 1e-9
+        assert np.array_equal(b.hard, a.hard ^ c)
+        assert a.cert == b.cert and a.alp_iters == b.alp_iters
+        assert np.array_equal(a.in_lp, b.in_lp)
+        for j in np.flatnonzero(a.in_lp):
+            cm = sum(1 << e for e, i in enumerate(code.row(j)) if c[i])
+            assert int(b.masks[j]) == int(a.masks[j]) ^ cm
+
+
+def test_ipm_vertex_matches_simplex():
+    """The interior-point solution, after vertex recovery, equals the
+    simplex vertex of the same LP (HiGHS), and satisfies the KKT system
+    (Eqs. 18-21) to the stopping tolerances."""
+    from scipy.optimize import linprog
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 1.5, 9, range(8))
+    prm = OracleParams()
+    checked = 0
+    for g in G:
+        res = oracle.decode(code, g)
+        for h in res.history:
+            L = lp.build(code, g, h.in_lp, h.masks)
+            r = ipm.solve(L.A, L.b, L.c, prm)
+            gap, fp, fd = ipm.convergence_measures(L.A, L.b, L.c, r.x, r.y, r.z)
+            assert r.status == 0 and gap < prm.tol_gap and fp < prm.tol_feas and fd < prm.tol_feas
+            xv, ok = vertex.recover(L.A, L.b, L.c, r.x, r.z)
+            ref = linprog(L.c, A_eq=L.A, b_eq=L.b, bounds=(0, None), method="highs-ds")
+            assert ok
+            assert np.max(np.abs(xv - ref.x)) < 1e-9
+            checked += 1
+    assert checked > 10
+
+
+def test_initial_lp_is_hard_decision_and_codeword_input():
+    """Eq. 8: with no cut violated, u = u^0 (the hard decision) and no LP
+    is solved."""
+    code = named_code("gallager_120")
+    g = np.abs(awgn_llr_frames(code.n, code.design_rate, 2.0, 0, [0])[0]) + 0.1
+    res = oracle.decode(code, g)
+    assert res.alp_iters == 0 and res.cert == 1
+    assert np.all(res.u == 0) and np.all(res.hard == 0)

@@ -1,0 +1,133 @@
+"""Pins for the oracle's MTS preconditioners (Algorithms 5-8), the M-solve
+and PCG (Algorithm 4): structural triangularity, the greedy rule of
+Algorithm 7 replayed step by step, dense-solve agreement, the exact
+one-step case M = Q, Lemma 2 and Theorem 5.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ipm, lp, mts
+from oracle.params import OracleParams
+from synth import awgn_llr_frames, named_code
+
+
+def lps_of_frames(n_frames=6, ebn0=2.0, seed=0):
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, ebn0, seed, range(n_frames))
+    out = []
+    for g in G:
+        res = oracle.decode(code, g)
+        for h in res.history:
+            out.append((code, g, lp.build(code, g, h.in_lp, h.masks), res.cert))
+    return out
+
+
+def test_colwise_is_upper_triangular_and_greedy():
+    rng = np.random.default_rng(1)
+    for code, g, L, _ in lps_of_frames()[:12]:
+        p, q = L.A.shape
+        w = np.exp(rng.normal(size=q) * 4)
+        col, row = mts.colwise(L.A, w)
+        assert len(set(col)) == p and sorted(row) == list(range(p))
+        T = L.A[np.ix_(row, col)]
+        assert np.allclose(np.tril(T, -1), 0)
+        assert np.all(np.abs(np.diag(T)) == 1)
+        # replay: at step k, col[k] is degree-1 in the residual matrix with
+        # its only nonzero in row[k], and no degree-1 column outweighs it
+        alive = np.ones(p, bool)
+        taken = np.zeros(q, bool)
+        for k in range(p):
+            deg = (L.A[alive] != 0).sum(axis=0)
+            deg1 = np.flatnonzero((deg == 1) & ~taken)
+            i = col[k]
+            assert i in deg1
+            assert np.flatnonzero(L.A[:, i] * alive)[0] == row[k]
+            best = max(deg1, key=lambda t: (w[t], -t))
+            assert best == i
+            alive[row[k]] = False
+            taken[i] = True
+
+
+def test_msolve_and_pcg_match_dense_solves():
+    rng = np.random.default_rng(2)
+    for code, g, L, _ in lps_of_frames()[:10]:
+        p, q = L.A.shape
+        d2 = np.exp(rng.normal(size=q) * 3)
+        col, row = mts.colwise(L.A, d2)
+        r = rng.normal(size=p)
+        AM = L.A[:, col]
+        M = AM @ np.diag(d2[col]) @ AM.T
+        z = mts.msolve(L.A, d2, col, row, r)
+        assert np.linalg.norm(M @ z - r) <= 1e-10 * np.linalg.norm(r) * max(1.0, np.linalg.norm(M))
+        Q = L.A @ np.diag(d2) @ L.A.T
+        x_ref = np.linalg.solve(Q, r)
+        x, it = mts.pcg(L.A, d2, r, col, row, 1e-12, 5 * p)
+        assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+
+
+def test_pcg_converges_in_one_step_when_m_equals_q():
+    """If d_i = 0 off the preconditioning set, M = A_M D_M^2 A_M' = Q and
+    the first PCG step is exact."""
+    rng = np.random.default_rng(3)
+    for code, g, L, _ in lps_of_frames()[:8]:
+        p, q = L.A.shape
+        d2 = np.exp(rng.normal(size=q))
+        col, row = mts.colwise(L.A, d2)
+        d2z = np.zeros(q)
+        d2z[col] = d2[col]
+        w = rng.normal(size=p)
+        res = []
+        x, it = mts.pcg(L.A, d2z, w, col, row, 1e-12, 10, residuals=res)
+        assert it <= 1 and res[-1] < 1e-12
+
+
+def test_triangulation_and_rowwise_structure():
+    rng = np.random.default_rng(4)
+    for code, g, L, _ in lps_of_frames()[:6]:
+        p, q = L.A.shape
+        w = rng.random(q)
+        col, row = mts.rowwise(L.A, w, code.n)
+        assert len(col) == p and sorted(row) == list(range(p))
+        T = L.A[np.ix_(row, col)]
+        assert np.allclose(np.triu(T, 1), 0) and np.all(np.abs(np.diag(T)) == 1)
+        tri = mts.triangulate(L.A, list(range(code.n, q)))     # slack set
+        assert tri is not None
+
+
+def test_lemma2_and_theorem5_on_integral_lps():
+    """Lemma 2: the basic set of an integral LP has no stopping set
+    (Algorithm 5 triangulates it). Theorem 5: near the optimum, the
+    incremental (Algorithm 6) and row-wise (Algorithm 8) sets contain it."""
+    prm = OracleParams()
+    checked = 0
+    for code, g, L, cert in lps_of_frames(10):
+        tr = []
+        r = ipm.solve(L.A, L.b, L.c, prm, trace=tr)
+        u = L.u_from_x(r.x)
+        if np.max(np.abs(u - np.round(u))) > 1e-6:
+            continue
+        basic = np.flatnonzero(r.x > r.z)
+        assert mts.triangulate(L.A, basic) is not None
+        d2 = r.x / r.z
+        col_i, _ = mts.incremental(L.A, d2)
+        col_r, _ = mts.rowwise(L.A, d2, code.n)
+        assert set(basic) <= set(col_i)
+        assert set(basic) <= set(col_r)
+        checked += 1
+        if checked >= 6:
+            break
+    assert checked >= 3
+
+
+def test_pcg_newton_solver_reproduces_cholesky_ipm():
+    """The IPM with PCG + column-wise MTS Newton solves ends at the same
+    vertex as with the direct (Cholesky) solve."""
+    prm = OracleParams()
+    for code, g, L, _ in lps_of_frames(3):
+        r1 = ipm.solve(L.A, L.b, L.c, prm)
+        r2 = ipm.solve(L.A, L.b, L.c, prm,
+                       solve_normal=mts.pcg_normal_solver(L.A, code.n, "colwise", 1e-10, 2000))
+        assert r2.status == 0
+        assert np.max(np.abs(L.u_from_x(r1.x) - L.u_from_x(r2.x))) < 1e-6
