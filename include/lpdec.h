@@ -1,0 +1,239 @@
+/*
+ * lpdec.h — C ABI of the GB300 (sm_103a) adaptive LP decoder.
+ *
+ * The library decodes binary linear codes by linear programming as in
+ * Taghavi, Shokrollahi, Siegel, "Efficient Implementation of Linear
+ * Programming Decoding":
+ *   - the code is given by its parity-check matrix H (m x n, Section II-A),
+ *     passed in CSR form;
+ *   - each frame is given by its LLR costs gamma (Eq. 4);
+ *   - the decoder runs MALP-A (Algorithm 3) or MALP-B (Section III-A), with
+ *     the O(d_j) cut search of Algorithm 2;
+ *   - every LP is solved by the infeasible primal-dual path-following
+ *     method of Section IV-B, whose normal equations (Eq. 24) are solved by
+ *     PCG (Algorithm 4) with the column-wise maximum-weight triangular-set
+ *     preconditioner (Section V, Algorithm 7);
+ *   - the result is the LP solution u, its hard decision and the ML
+ *     certificate flag (Section II-B: an integral u is the ML codeword).
+ *
+ * All work runs in CUDA kernels on one GPU. There is no CPU fallback: every
+ * entry point that computes returns LPDEC_ERR_CUDA or LPDEC_ERR_NO_DEVICE
+ * when no usable device is present.
+ *
+ * Conventions
+ *   - Return value: 0 (LPDEC_OK) or a negative LPDEC_ERR_* code. No C++
+ *     exception crosses this boundary.
+ *   - "host" pointers are ordinary CPU memory owned by the caller; the call
+ *     copies inputs before it returns and has written outputs when it
+ *     returns. "device" pointers are CUDA global memory of the context's
+ *     device, owned by the caller; *_device entry points are asynchronous
+ *     on the given stream (a cudaStream_t passed as void*, NULL = legacy
+ *     default stream) and the caller synchronises.
+ *   - Frame-major layout: array "[nframes x n]" holds frame f at offset f*n.
+ *   - Cut masks: for check j, bit e of mask[j] is set iff the e-th
+ *     neighbour of j (in the CSR column order of row j) belongs to the odd
+ *     set V of j's parity inequality (Eq. 5). mask[j] = 0 when j has no
+ *     inequality in the final LP. Check degrees must be <= 32.
+ */
+#ifndef LPDEC_H
+#define LPDEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes (return values and lpdec_stats.status). */
+#define LPDEC_OK                 0
+#define LPDEC_ERR_INVALID_ARG   -1  /* bad size, CSR, degree > 32, non-finite gamma */
+#define LPDEC_ERR_OUT_OF_BUDGET -2  /* request exceeds the context's HBM budget */
+#define LPDEC_ERR_NOT_CONVERGED -3  /* an iteration cap was reached (per frame) */
+#define LPDEC_ERR_TIMEOUT       -4  /* a bounded wait expired */
+#define LPDEC_ERR_PENDING       -5  /* result not ready yet */
+#define LPDEC_ERR_CUDA          -6  /* a CUDA runtime call failed */
+#define LPDEC_ERR_NO_DEVICE     -7  /* no CUDA device / unsupported architecture */
+
+/* Adaptive-LP variants (Section III-A). */
+#define LPDEC_MALP_A 0
+#define LPDEC_MALP_B 1
+
+/* Arithmetic of the PCG solve (the IPM state is always FP64). */
+#define LPDEC_FP64  0   /* FP64 PCG */
+#define LPDEC_MIXED 1   /* FP32 PCG inner solves refined against FP64 residuals */
+
+/*
+ * Tolerances and rules the paper leaves open (its Section VII lists the
+ * stopping criteria and step sizes as future work). Defaults from
+ * lpdec_default_params():
+ *   sigma    = 0.1    centering: mu = sigma * x'z / q (Eq. 28 with sigma)
+ *   eta      = 0.99   step length = min(1, eta * step to the boundary)
+ *   tol_gap  = 1e-8   stop when x'z / (1 + |c'x|) < tol_gap
+ *   tol_feas = 1e-8   ... and ||r_b||/(1+||b||), ||r_c||/(1+||c||) < tol_feas
+ *   tol_pcg  = 1e-10  floor of the Newton-solve tolerance ||r||_2 / ||w||_2
+ *   pcg_gap_factor = 0.01  inexact Newton: tolerance max(tol_pcg, min(1e-3, 0.01 * gap))
+ *   tol_inner = 1e-5  relative tolerance of each FP32 PCG round (LPDEC_MIXED)
+ *   tol_feas_loose = 1e-6  the IPM also stops when the gap is below tol_gap and
+ *                     both infeasibilities are below this (limited accuracy of
+ *                     the Newton solves near the optimum)
+ *   tau_act  = 1e-9   an inequality is active iff its slack <= tau_act
+ *   tau_cut  = 1e-9   a check is violated iff Eq. 6's left side < 1 - tau_cut
+ *   tau_int  = 1e-9   u is integral iff max |u_i - round(u_i)| <= tau_int
+ *   max_alp = 200, max_ipm = 200, max_pcg = 2000 iteration caps (max_pcg per
+ *                     Newton solve, over all refinement rounds)
+ *   variant = LPDEC_MALP_A, precision = LPDEC_FP64
+ * The decisions are taken on the LP's optimal vertex, recovered from the
+ * final interior-point iterate through its strictly complementary
+ * partition (basic iff x_i > z_i, Section VI-A).
+ */
+typedef struct lpdec_params {
+    double sigma, eta, tol_gap, tol_feas, tol_pcg, tau_act, tau_cut, tau_int;
+    double pcg_gap_factor;  /* Newton solve tolerance = max(tol_pcg, min(1e-3, f * gap)) */
+    double tol_inner;       /* relative tolerance of one FP32 PCG round (LPDEC_MIXED) */
+    double tol_feas_loose;  /* infeasibility accepted once the gap is below tol_gap */
+    int32_t max_alp, max_ipm, max_pcg, variant, precision;
+    int32_t threads_per_block;  /* 0 = library choice */
+    int32_t smem_budget;        /* bytes of shared memory per CTA, 0 = library choice */
+    int32_t reserved;
+} lpdec_params;
+
+/* Per-frame results besides u / hard / cert. */
+typedef struct lpdec_stats {
+    int32_t status;           /* LPDEC_OK or LPDEC_ERR_NOT_CONVERGED / INVALID_ARG */
+    int32_t alp_iters;        /* number of LPs solved (0 if the hard decision is a codeword) */
+    int32_t ipm_iters_total;  /* interior-point iterations over all LPs */
+    int32_t pcg_iters_total;  /* PCG iterations over all Newton steps */
+    int32_t lp_rows_final;    /* p of the last LP (parity inequalities) */
+    int32_t vertex_failures;  /* LPs whose optimal-vertex recovery was rejected */
+    int32_t max_levels;       /* deepest triangular-solve level schedule seen */
+    int32_t reserved;
+    double  objective;        /* gamma'u */
+} lpdec_stats;
+
+typedef struct lpdec_ctx lpdec_ctx;    /* opaque: device, streams, scratch */
+typedef struct lpdec_code lpdec_code;  /* opaque: device copy of H (CSR + CSC) */
+
+/* Fills *p with the defaults listed above. */
+void lpdec_default_params(lpdec_params* p);
+
+/* Static string for a status code. */
+const char* lpdec_error_string(int32_t code);
+
+/* Host-only (no device needed): the per-frame workspace of a code with m
+ * checks, n bits and E edges in the given precision mode — shared memory
+ * per CTA (*smem_bytes) and global scratch per concurrently decoded frame
+ * (*global_bytes_per_frame) — for a shared-memory budget per CTA
+ * (smem_budget <= 0: the default). Also validates the layout (every array
+ * aligned, inside its region, disjoint from the others). */
+int32_t lpdec_workspace_bytes(int32_t m, int32_t n, int32_t E, int32_t precision,
+                              int32_t smem_budget, size_t* smem_bytes,
+                              size_t* global_bytes_per_frame);
+
+/* Creates a context on CUDA device `device`. `params` may be NULL
+ * (defaults). `hbm_budget_bytes` bounds the scratch the context may hold
+ * (0 = no bound). Returns LPDEC_ERR_NO_DEVICE without a usable device. */
+int32_t lpdec_ctx_create(int32_t device, const lpdec_params* params,
+                         size_t hbm_budget_bytes, lpdec_ctx** out);
+void lpdec_ctx_destroy(lpdec_ctx* ctx);
+
+/* Replaces the context's parameters (takes effect at the next call). */
+int32_t lpdec_ctx_set_params(lpdec_ctx* ctx, const lpdec_params* params);
+
+/* Uploads H (m x n) given in CSR form on the host: row_ptr[m+1],
+ * col_idx[row_ptr[m]] with strictly increasing columns in each row.
+ * Validates the CSR, that every row has 1..32 entries and that
+ * m, n <= 32767 (the kernels pack indices into 15 bits). */
+int32_t lpdec_code_create(lpdec_ctx* ctx, int32_t m, int32_t n,
+                          const int32_t* row_ptr, const int32_t* col_idx,
+                          lpdec_code** out);
+void lpdec_code_destroy(lpdec_code* code);
+
+/* Decodes one frame (host pointers). gamma[n] in; u_out[n], hard_out[n],
+ * cert_out[1] out; cut_mask_out[m] and stats optional (NULL). */
+int32_t lpdec_decode(lpdec_ctx* ctx, const lpdec_code* code, const double* gamma,
+                     double* u_out, uint8_t* hard_out, int32_t* cert_out,
+                     uint32_t* cut_mask_out, lpdec_stats* stats);
+
+/* Decodes nframes frames of one code (host pointers, frame-major):
+ * gamma[nframes x n] in; u_out[nframes x n], hard_out[nframes x n],
+ * cert_out[nframes] out; cut_mask_out[nframes x m] and stats[nframes]
+ * optional. Copies in and out inside the call. */
+int32_t lpdec_decode_batch(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                           const double* gamma, double* u_out, uint8_t* hard_out,
+                           int32_t* cert_out, uint32_t* cut_mask_out,
+                           lpdec_stats* stats);
+
+/* Same as lpdec_decode_batch with DEVICE pointers, asynchronous on
+ * `stream`. d_cut_mask and d_stats may be NULL. One persistent kernel
+ * decodes all frames; CTAs take frames from a queue. */
+int32_t lpdec_decode_batch_device(lpdec_ctx* ctx, const lpdec_code* code,
+                                  int32_t nframes, const double* d_gamma,
+                                  double* d_u, uint8_t* d_hard, int32_t* d_cert,
+                                  uint32_t* d_cut_mask, lpdec_stats* d_stats,
+                                  void* stream);
+
+/* ---- Single steps of the hot path (device pointers, asynchronous) ----
+ * These run the same device code as the decoder on caller-given state, one
+ * frame per CTA, so each step can be checked on its own. "LP state" means
+ * in_lp[nframes x m] (1 = check j has a parity inequality in the LP) and
+ * mask[nframes x m]; the LP rows are the checks with in_lp = 1 in
+ * increasing order, p = their count, q = n + p, columns n..n+p-1 are the
+ * slacks (Eq. 16). Per-frame vectors over columns use a stride of n + m
+ * (q <= n + m), over rows a stride of m. */
+
+/* One round of the MALP-A / MALP-B search (Algorithm 3, lines 5-10, with
+ * Algorithm 2 per check) at u[nframes x n]. active[nframes x m] marks
+ * checks whose inequality is active in the current LP. mask and in_lp are
+ * updated in place; flag[nframes] = 1 if an inequality was added. */
+int32_t lpdec_cut_search_device(lpdec_ctx* ctx, const lpdec_code* code,
+                                int32_t nframes, const double* d_u,
+                                const uint8_t* d_active, uint8_t* d_in_lp,
+                                uint32_t* d_mask, int32_t* d_flag, void* stream);
+
+/* Column-wise greedy MTS (Algorithm 7) of the LP given by (gamma, in_lp,
+ * mask) with column weights w[nframes x (n+m)] (the decoder uses
+ * w_i = d_i^2 = x_i / z_i; ties go to the lower column index). Writes the
+ * selection order: col[nframes x m] (column chosen at step k) and
+ * row[nframes x m] (its LP row); entries k >= p are -1. */
+int32_t lpdec_mts_select_device(lpdec_ctx* ctx, const lpdec_code* code,
+                                int32_t nframes, const double* d_gamma,
+                                const uint8_t* d_in_lp, const uint32_t* d_mask,
+                                const double* d_w, int32_t* d_col, int32_t* d_row,
+                                void* stream);
+
+/* PCG (Algorithm 4) with the Algorithm 7 preconditioner (weights d2) for
+ * (A D^2 A') dy = w of the LP given by (gamma, in_lp, mask):
+ * d2[nframes x (n+m)], w[nframes x m] in; dy[nframes x m] and
+ * iters[nframes] out. Runs in the context's precision mode. */
+int32_t lpdec_pcg_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                         const double* d_gamma, const uint8_t* d_in_lp,
+                         const uint32_t* d_mask, const double* d_d2,
+                         const double* d_w, double* d_dy, int32_t* d_iters,
+                         void* stream);
+
+/* Solves one LP (Section IV-B interior-point method + optimal-vertex
+ * recovery) given by (gamma, in_lp, mask): x[nframes x (n+m)] out (the
+ * recovered vertex, slacks at n..n+p-1), stats[nframes] out
+ * (ipm_iters_total, pcg_iters_total, vertex_failures, status, objective). */
+int32_t lpdec_lp_solve_device(lpdec_ctx* ctx, const lpdec_code* code,
+                              int32_t nframes, const double* d_gamma,
+                              const uint8_t* d_in_lp, const uint32_t* d_mask,
+                              double* d_x, lpdec_stats* d_stats, void* stream);
+
+/* Diagnostic form of lpdec_lp_solve_device: also writes, per frame and per
+ * interior-point iteration k < max_trace, 8 doubles to
+ * trace[(f * max_trace + k) * 8 ...]: relative gap, relative primal and dual
+ * infeasibility, PCG iterations, final PCG relative residual, beta_P,
+ * beta_D, and the deepest triangular-solve level schedule. */
+int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code,
+                                    int32_t nframes, const double* d_gamma,
+                                    const uint8_t* d_in_lp, const uint32_t* d_mask,
+                                    double* d_x, lpdec_stats* d_stats,
+                                    double* d_trace, int32_t max_trace, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPDEC_H */

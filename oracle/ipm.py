@@ -18,8 +18,8 @@ Readings (``OracleParams``): sigma = 0.1 scales Eq. 28; each step length is
 min(1, eta * largest step to the boundary of its own cone); the infeasible
 variant may start anywhere with x, z > 0, and the oracle starts every LP
 cold at x = e, y = 0, z = c + e; the stopping tests are relative:
-x'z/(1+|c'x|) < tol_gap, ||r_b||/(1+||b||) < tol_feas,
-||r_c||/(1+||c||) < tol_feas.
+x'z/(1+|c'x|) < tol_gap with ||r_b||/(1+||b||) and ||r_c||/(1+||c||) both
+below tol_feas (or both below tol_feas_loose).
 
 The normal equations are solved by a dense Cholesky factorisation of
 A D^2 A' (Section IV-C names it as the direct method), so this oracle does not
@@ -116,7 +116,8 @@ def solve(A, b, c, params: OracleParams | None = None, solve_normal=None,
     gap = fp = fd = np.inf
     for it in range(prm.max_ipm + 1):
         gap, fp, fd = convergence_measures(A, b, c, x, y, z)
-        if gap < prm.tol_gap and fp < prm.tol_feas and fd < prm.tol_feas:
+        if gap < prm.tol_gap and ((fp < prm.tol_feas and fd < prm.tol_feas) or
+                                  (fp < prm.tol_feas_loose and fd < prm.tol_feas_loose)):
             status = OK
             break
         if it == prm.max_ipm:

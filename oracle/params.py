@@ -11,7 +11,10 @@ tests pass identical values to both sides explicitly.
   eta       fraction of the step to the boundary (Section IV-B asks only
             that x, z stay nonnegative): beta_P = min(1, eta * max step).
   tol_gap   stop when x'z / (1 + |c'x|) < tol_gap  (Section IV-B, end).
-  tol_feas  ... and ||r_b||/(1+||b||) < tol_feas, ||r_c||/(1+||c||) < tol_feas.
+  tol_feas  ... and ||r_b||/(1+||b||) < tol_feas, ||r_c||/(1+||c||) < tol_feas;
+            or, once the gap test holds, both below tol_feas_loose (the
+            Newton solves lose accuracy as D^2 spreads near the optimum; the
+            optimal vertex is recovered from the iterate either way).
   tol_pcg   PCG stops when ||w - Q dy||_2 / ||w||_2 < tol_pcg.
   tau_act   a cut is active iff its slack x_{n+j} <= tau_act (the paper's
             "slack variable is zero", Section III-A), read on the optimal
@@ -38,6 +41,7 @@ class OracleParams:
     eta: float = 0.99
     tol_gap: float = 1e-8
     tol_feas: float = 1e-8
+    tol_feas_loose: float = 1e-6
     tol_pcg: float = 1e-10
     tau_act: float = 1e-9
     tau_cut: float = 1e-9

@@ -1,0 +1,768 @@
+// Kernels and host C ABI of the adaptive LP decoder (see include/lpdec.h).
+//
+// Build: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -shared -Xcompiler -fPIC
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lpdec_device.cuh"
+
+using namespace lpdec;
+
+// ---------------------------------------------------------------------------
+// Kernels. All are persistent: CTAs take frames from a queue counter.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct KernelShared {
+    double red[128];
+    int shscan[40];
+    int next;
+};
+
+__device__ __forceinline__ int next_frame(Blk& B, int* counter, int* slot) {
+    if (B.tid == 0) *slot = atomicAdd(counter, 1);
+    __syncthreads();
+    int f = *slot;
+    __syncthreads();
+    return f;
+}
+
+#define KERNEL_PROLOGUE                                                         \
+    extern __shared__ __align__(16) char smem[];                                \
+    __shared__ KernelShared ks;                                                 \
+    Blk B{(int)threadIdx.x, (int)blockDim.x, (int)(threadIdx.x & 31),          \
+          (int)(threadIdx.x >> 5), (int)(blockDim.x >> 5), ks.red, 0};          \
+    WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.gbytes, C.n, C.m, (int)L.q2);
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_decode(CodeView C, DevParams P, Layout L, const double* __restrict__ gamma,
+         double* u, uint8_t* hard, int32_t* cert, uint32_t* mask, lpdec_stats* stats,
+         int nframes, int* counter, char* gscratch) {
+    KERNEL_PROLOGUE
+    for (;;) {
+        int f = next_frame(B, counter, &ks.next);
+        if (f >= nframes) break;
+        FrameOut o{u + (size_t)f * C.n, hard + (size_t)f * C.n, cert + f,
+                   mask ? mask + (size_t)f * C.m : nullptr, stats ? stats + f : nullptr};
+        decode_frame<T>(B, C, W, P, gamma + (size_t)f * C.n, o, (int)L.q2, ks.shscan);
+    }
+}
+
+// flip bits from gamma, flags/mask from the caller's LP state
+template <typename T>
+__device__ inline void load_lp_state(Blk& B, const CodeView& C, WS<T>& W, const double* g,
+                                     const uint8_t* in_lp, const uint32_t* mask) {
+    for (int k = B.tid; k < (C.n + 31) / 32; k += B.nt) {
+        uint32_t bits = 0;
+        for (int b = 0; b < 32; ++b) {
+            int i = k * 32 + b;
+            if (i < C.n && g[i] < 0.0) bits |= 1u << b;
+        }
+        W.flip[k] = bits;
+    }
+    for (int j = B.tid; j < C.m; j += B.nt) {
+        W.flags[j] = in_lp[j] ? kInLP : 0;
+        W.mask[j] = mask[j];
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_cut_search(CodeView C, DevParams P, Layout L, const double* u, const uint8_t* active,
+             uint8_t* in_lp, uint32_t* mask, int32_t* flag, int nframes, int* counter,
+             char* gscratch) {
+    KERNEL_PROLOGUE
+    for (;;) {
+        int f = next_frame(B, counter, &ks.next);
+        if (f >= nframes) break;
+        const size_t om = (size_t)f * C.m;
+        for (int i = B.tid; i < C.n; i += B.nt) W.u[i] = u[(size_t)f * C.n + i];
+        for (int j = B.tid; j < C.m; j += B.nt) {
+            uint8_t fl = in_lp[om + j] ? kInLP : 0;
+            if (fl && active[om + j]) fl |= kActive;
+            W.flags[j] = fl;
+            W.mask[j] = mask[om + j];
+        }
+        __syncthreads();
+        if (P.variant == LPDEC_MALP_B) drop_inactive<T>(B, C, W);
+        int added = cut_search<T>(B, C, W, P);
+        for (int j = B.tid; j < C.m; j += B.nt) {
+            in_lp[om + j] = (W.flags[j] & kInLP) ? 1 : 0;
+            mask[om + j] = W.mask[j];
+        }
+        if (B.tid == 0) flag[f] = added;
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_mts_select(CodeView C, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
+             const uint32_t* mask, const double* wts, int32_t* col, int32_t* row,
+             int nframes, int* counter, char* gscratch) {
+    KERNEL_PROLOGUE
+    const int qm = C.n + C.m;
+    for (;;) {
+        int f = next_frame(B, counter, &ks.next);
+        if (f >= nframes) break;
+        load_lp_state<T>(B, C, W, gamma + (size_t)f * C.n, in_lp + (size_t)f * C.m,
+                         mask + (size_t)f * C.m);
+        Frame F{0, C.n, 0.0, 0.0};
+        lp_build<T>(B, C, W, F, ks.shscan);
+        for (int i = B.tid; i < F.q; i += B.nt) W.d2[i] = wts[(size_t)f * qm + i];
+        __syncthreads();
+        mts_select<T>(B, C, W, F, W.d2, (int)L.q2);
+        selection_order<T>(B, W, F, col + (size_t)f * C.m, row + (size_t)f * C.m, C.m);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_pcg(CodeView C, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
+      const uint32_t* mask, const double* d2, const double* wv, double* dy, int32_t* iters,
+      int nframes, int* counter, char* gscratch) {
+    KERNEL_PROLOGUE
+    const int qm = C.n + C.m;
+    for (;;) {
+        int f = next_frame(B, counter, &ks.next);
+        if (f >= nframes) break;
+        load_lp_state<T>(B, C, W, gamma + (size_t)f * C.n, in_lp + (size_t)f * C.m,
+                         mask + (size_t)f * C.m);
+        Frame F{0, C.n, 0.0, 0.0};
+        lp_build<T>(B, C, W, F, ks.shscan);
+        for (int i = B.tid; i < F.q; i += B.nt) W.d2[i] = d2[(size_t)f * qm + i];
+        for (int r = B.tid; r < F.p; r += B.nt) W.w[r] = wv[(size_t)f * C.m + r];
+        __syncthreads();
+        Levels Lv = mts_select<T>(B, C, W, F, W.d2, (int)L.q2);
+        for (int i = B.tid; i < F.q; i += B.nt) W.d2t[i] = (T)W.d2[i];
+        for (int r = B.tid; r < F.p; r += B.nt) W.invd2p[r] = (T)(1.0 / W.d2[W.pivcol[r]]);
+        __syncthreads();
+        NewtonOut no = newton_solve<T>(B, C, W, F, Lv, P, P.tol_pcg, P.max_pcg);
+        for (int r = B.tid; r < C.m; r += B.nt) dy[(size_t)f * C.m + r] = r < F.p ? W.dy[r] : 0.0;
+        if (B.tid == 0) iters[f] = no.iters;
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_lp_solve(CodeView C, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
+           const uint32_t* mask, double* xo, lpdec_stats* stats, int nframes, int* counter,
+           char* gscratch, double* trace, int max_trace) {
+    KERNEL_PROLOGUE
+    const int qm = C.n + C.m;
+    for (;;) {
+        int f = next_frame(B, counter, &ks.next);
+        if (f >= nframes) break;
+        const double* g = gamma + (size_t)f * C.n;
+        load_lp_state<T>(B, C, W, g, in_lp + (size_t)f * C.m, mask + (size_t)f * C.m);
+        Frame F{0, C.n, 0.0, 0.0};
+        lp_build<T>(B, C, W, F, ks.shscan);
+        lpdec_stats st{};
+        if (F.p > 0) {
+            IpmOut io = ipm_solve<T>(B, C, W, F, P, g, (int)L.q2,
+                                     trace ? trace + (size_t)f * 8 * max_trace : nullptr,
+                                     max_trace);
+            st.vertex_failures = vertex_recover<T>(B, C, W, F, g);
+            st.ipm_iters_total = io.iters;
+            st.pcg_iters_total = io.pcg_iters;
+            st.max_levels = io.max_levels;
+            st.status = io.converged ? LPDEC_OK : LPDEC_ERR_NOT_CONVERGED;
+        } else {
+            for (int i = B.tid; i < C.n; i += B.nt) W.x[i] = 0.0;
+            __syncthreads();
+        }
+        st.lp_rows_final = F.p;
+        double obj = 0.0;
+        for (int i = B.tid; i < qm; i += B.nt) {
+            double v = i < F.q ? W.x[i] : 0.0;
+            xo[(size_t)f * qm + i] = v;
+            if (i < C.n) obj += g[i] * (flipped(W.flip, i) ? 1.0 - v : v);
+        }
+        obj = bsum(B, obj);
+        if (B.tid == 0) { st.objective = obj; stats[f] = st; }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct lpdec_ctx {
+    int device = 0;
+    lpdec_params prm{};
+    size_t budget = 0;
+    int sm_count = 0;
+    int smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    char* gscratch = nullptr;
+    size_t gscratch_bytes = 0;
+    int* counter = nullptr;
+    char* staging = nullptr;     // device buffers of the host entry points
+    size_t staging_bytes = 0;
+    std::mutex mu;
+};
+
+struct lpdec_code {
+    lpdec_ctx* ctx = nullptr;
+    int m = 0, n = 0, E = 0;
+    int *h_ptr = nullptr, *h_col = nullptr, *e_chk = nullptr;
+    int *v_ptr = nullptr, *v_chk = nullptr, *v_eidx = nullptr;
+};
+
+namespace {
+
+thread_local char g_err[256];
+
+#define CK(call)                                                                \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            snprintf(g_err, sizeof g_err, "%s: %s", #call, cudaGetErrorString(e_)); \
+            return LPDEC_ERR_CUDA;                                              \
+        }                                                                       \
+    } while (0)
+
+DevParams to_dev(const lpdec_params& p) {
+    DevParams d;
+    d.sigma = p.sigma; d.eta = p.eta; d.tol_gap = p.tol_gap; d.tol_feas = p.tol_feas;
+    d.tol_pcg = p.tol_pcg; d.tau_act = p.tau_act; d.tau_cut = p.tau_cut; d.tau_int = p.tau_int;
+    d.pcg_gap_factor = p.pcg_gap_factor; d.tol_inner = p.tol_inner;
+    d.tol_feas_loose = p.tol_feas_loose;
+    d.max_alp = p.max_alp; d.max_ipm = p.max_ipm; d.max_pcg = p.max_pcg;
+    d.variant = p.variant; d.precision = p.precision;
+    return d;
+}
+
+CodeView view_of(const lpdec_code* c) {
+    CodeView v;
+    v.n = c->n; v.m = c->m; v.E = c->E;
+    v.h_ptr = c->h_ptr; v.h_col = c->h_col; v.e_chk = c->e_chk;
+    v.v_ptr = c->v_ptr; v.v_chk = c->v_chk; v.v_eidx = c->v_eidx;
+    return v;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Every array of the layout lies inside its region (shared or global), is
+// 16-byte aligned and overlaps no other array.
+bool layout_ok(const Layout& L, const std::vector<size_t>& sizes) {
+    struct Iv { size_t a, b; bool g; };
+    std::vector<Iv> iv;
+    for (int k = 0; k < A_COUNT; ++k) {
+        bool g = (L.off[k] & kGlobalBit) != 0;
+        size_t a = L.off[k] & ~kGlobalBit;
+        if (a % 16) return false;
+        iv.push_back({a, a + sizes[k], g});
+        if (!g && a + sizes[k] > L.smem_bytes) return false;
+        if (g && a + sizes[k] > L.gbytes) return false;
+    }
+    for (size_t i = 0; i < iv.size(); ++i)
+        for (size_t j = i + 1; j < iv.size(); ++j)
+            if (iv[i].g == iv[j].g && iv[i].a < iv[j].b && iv[j].a < iv[i].b &&
+                iv[i].b > iv[i].a && iv[j].b > iv[j].a)
+                return false;
+    return true;
+}
+
+// Lays the workspace out. Hot arrays (everything the PCG loop and the MTS
+// selection touch) go to shared memory in priority order while they fit the
+// budget; the bitmap and the level pointer arrays, which the kernels update
+// with shared-memory atomics, always do. The FP64 interior-point state goes
+// to per-CTA global scratch.
+Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes) {
+    const size_t q = (size_t)n + m;
+    size_t q2 = 1;
+    while (q2 < q) q2 <<= 1;
+    const size_t vec = std::max(real_bytes * vec_elems(n, m), 8 * q2 + 4 * q);
+    struct Spec { int id; size_t bytes; int where; };  // 0 = budgeted, 1 = always shared, 2 = global
+    const size_t D = 8, I = 4, H = 2;
+    std::vector<Spec> specs = {
+        {S_BITMAP, I * ((q + 31) / 32), 1}, {S_LBPTR, I * (m + 2), 1}, {S_LFPTR, I * (m + 2), 1},
+        {S_CUR, I * (m + 2), 1},
+        {S_VEC, vec, 0}, {S_ROWENT, H * E, 0}, {S_COLENT, H * E, 0}, {S_PIVROW, H * q, 0},
+        {S_PIVCOL, H * m, 0}, {S_ROWCHK, H * m, 0}, {S_CHKROW, H * m, 0}, {S_PSGN, (size_t)m, 0},
+        {S_LBROWS, H * m, 0}, {S_LFROWS, H * m, 0}, {S_LB, H * m, 0}, {S_LF, H * m, 0},
+        {S_SELROW, H * m, 0}, {S_DEG, q, 0}, {S_FLAGS, (size_t)m, 0}, {S_MASK, I * m, 0},
+        {S_FLIP, I * ((n + 31) / 32), 0},
+        {G_X, D * q, 2}, {G_Z, D * q, 2}, {G_RC, D * q, 2}, {G_D2, D * q, 2}, {G_Y, D * m, 2},
+        {G_B, D * m, 2}, {G_W, D * m, 2}, {G_DY, D * m, 2}, {G_R64, D * m, 2}, {G_U, D * n, 2},
+        {G_T64, D * n, 2}, {G_BASIC, q, 2},
+    };
+    Layout L{};
+    size_t s = 0, g = 0;
+    std::vector<size_t> sizes(A_COUNT, 0);
+    for (const auto& sp : specs) {
+        size_t b = align_up(sp.bytes, 16);
+        sizes[sp.id] = sp.bytes;
+        if (sp.where == 1 || (sp.where == 0 && s + b <= budget)) {
+            L.off[sp.id] = (uint32_t)s;
+            s += b;
+        } else {
+            L.off[sp.id] = (uint32_t)g | kGlobalBit;
+            g += b;
+        }
+    }
+    L.smem_bytes = (uint32_t)s;
+    L.q2 = (uint32_t)q2;
+    L.gbytes = align_up(g, 256);
+    if (specs.size() != (size_t)A_COUNT || !layout_ok(L, sizes)) L.smem_bytes = 0xffffffffu;
+    return L;
+}
+
+struct Launch {
+    Layout L;
+    int threads;
+    int grid;
+};
+
+template <typename K>
+int32_t plan(lpdec_ctx* ctx, const lpdec_code* code, int nframes, K kernel, size_t real_bytes,
+             Launch* out) {
+    int threads = ctx->prm.threads_per_block > 0 ? ctx->prm.threads_per_block : 128;
+    threads = std::max(32, std::min(512, threads / 32 * 32));
+    size_t cap = (size_t)ctx->smem_optin - sizeof(KernelShared) - 1024;
+    size_t budget = ctx->prm.smem_budget > 0 ? std::min((size_t)ctx->prm.smem_budget, cap) : cap;
+    Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes);
+    if (L.smem_bytes == 0xffffffffu) {
+        snprintf(g_err, sizeof g_err, "inconsistent workspace layout");
+        return LPDEC_ERR_INVALID_ARG;
+    }
+    if (L.smem_bytes + sizeof(KernelShared) > (size_t)ctx->smem_optin) {
+        snprintf(g_err, sizeof g_err, "frame needs %u bytes of shared memory", L.smem_bytes);
+        return LPDEC_ERR_INVALID_ARG;
+    }
+    CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, L.smem_bytes));
+    if (per_sm < 1) {
+        snprintf(g_err, sizeof g_err, "kernel does not fit on an SM");
+        return LPDEC_ERR_INVALID_ARG;
+    }
+    int grid = std::max(1, std::min(nframes, per_sm * ctx->sm_count));
+    size_t need = (size_t)grid * L.gbytes;
+    if (need > ctx->gscratch_bytes) {
+        if (ctx->budget && need + ctx->staging_bytes > ctx->budget) return LPDEC_ERR_OUT_OF_BUDGET;
+        if (ctx->gscratch) CK(cudaFree(ctx->gscratch));
+        ctx->gscratch = nullptr;
+        ctx->gscratch_bytes = 0;
+        CK(cudaMalloc(&ctx->gscratch, need));
+        ctx->gscratch_bytes = need;
+    }
+    out->L = L;
+    out->threads = threads;
+    out->grid = grid;
+    return LPDEC_OK;
+}
+
+int32_t staging(lpdec_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->staging_bytes) return LPDEC_OK;
+    if (ctx->budget && bytes + ctx->gscratch_bytes > ctx->budget) return LPDEC_ERR_OUT_OF_BUDGET;
+    if (ctx->staging) CK(cudaFree(ctx->staging));
+    ctx->staging = nullptr;
+    ctx->staging_bytes = 0;
+    CK(cudaMalloc(&ctx->staging, bytes));
+    ctx->staging_bytes = bytes;
+    return LPDEC_OK;
+}
+
+int32_t check_ctx_code(lpdec_ctx* ctx, const lpdec_code* code) {
+    if (!ctx || !code || code->ctx != ctx) {
+        snprintf(g_err, sizeof g_err, "null or mismatched context/code");
+        return LPDEC_ERR_INVALID_ARG;
+    }
+    CK(cudaSetDevice(ctx->device));
+    return LPDEC_OK;
+}
+
+int32_t launch_decode(lpdec_ctx* ctx, const lpdec_code* code, int nframes, const double* d_gamma,
+                      double* d_u, uint8_t* d_hard, int32_t* d_cert, uint32_t* d_mask,
+                      lpdec_stats* d_stats, cudaStream_t s) {
+    if (nframes == 0) return LPDEC_OK;
+    Launch ln;
+    const bool mixed = ctx->prm.precision == LPDEC_MIXED;
+    int32_t rc = mixed ? plan(ctx, code, nframes, k_decode<float>, 4, &ln)
+                       : plan(ctx, code, nframes, k_decode<double>, 8, &ln);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
+    if (mixed)
+        k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+            view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
+            nframes, ctx->counter, ctx->gscratch);
+    else
+        k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+            view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
+            nframes, ctx->counter, ctx->gscratch);
+    CK(cudaGetLastError());
+    return LPDEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lpdec_default_params(lpdec_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->sigma = 0.1;
+    p->eta = 0.99;
+    p->tol_gap = 1e-8;
+    p->tol_feas = 1e-8;
+    p->tol_pcg = 1e-10;
+    p->tau_act = 1e-9;
+    p->tau_cut = 1e-9;
+    p->tau_int = 1e-9;
+    p->pcg_gap_factor = 0.01;
+    p->tol_inner = 1e-5;
+    p->tol_feas_loose = 1e-6;
+    p->max_alp = 200;
+    p->max_ipm = 200;
+    p->max_pcg = 2000;
+    p->variant = LPDEC_MALP_A;
+    p->precision = LPDEC_FP64;
+}
+
+const char* lpdec_error_string(int32_t code) {
+    switch (code) {
+        case LPDEC_OK: return "ok";
+        case LPDEC_ERR_INVALID_ARG: return "invalid argument";
+        case LPDEC_ERR_OUT_OF_BUDGET: return "out of HBM budget";
+        case LPDEC_ERR_NOT_CONVERGED: return "iteration cap reached";
+        case LPDEC_ERR_TIMEOUT: return "timeout";
+        case LPDEC_ERR_PENDING: return "pending";
+        case LPDEC_ERR_CUDA: return g_err[0] ? g_err : "CUDA error";
+        case LPDEC_ERR_NO_DEVICE: return "no usable CUDA device";
+        default: return "unknown status";
+    }
+}
+
+int32_t lpdec_workspace_bytes(int32_t m, int32_t n, int32_t E, int32_t precision,
+                              int32_t smem_budget, size_t* smem_bytes,
+                              size_t* global_bytes_per_frame) {
+    if (m <= 0 || n <= 0 || m > 32767 || n > 32767 || E <= 0 || E > 32 * m ||
+        (precision != LPDEC_FP64 && precision != LPDEC_MIXED))
+        return LPDEC_ERR_INVALID_ARG;
+    size_t budget = smem_budget > 0 ? (size_t)smem_budget : (size_t)227 * 1024;
+    Layout L = make_layout(n, m, E, budget, precision == LPDEC_MIXED ? 4 : 8);
+    if (L.smem_bytes == 0xffffffffu) return LPDEC_ERR_INVALID_ARG;
+    if (smem_bytes) *smem_bytes = L.smem_bytes + sizeof(KernelShared);
+    if (global_bytes_per_frame) *global_bytes_per_frame = (size_t)L.gbytes;
+    return LPDEC_OK;
+}
+
+int32_t lpdec_ctx_create(int32_t device, const lpdec_params* params, size_t hbm_budget_bytes,
+                         lpdec_ctx** out) {
+    if (!out) return LPDEC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= device || device < 0) {
+        cudaGetLastError();
+        snprintf(g_err, sizeof g_err, "no CUDA device %d", device);
+        return LPDEC_ERR_NO_DEVICE;
+    }
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, device));
+    if (prop.major < 10) {
+        snprintf(g_err, sizeof g_err, "device %d is sm_%d%d; this build targets sm_103a",
+                 device, prop.major, prop.minor);
+        return LPDEC_ERR_NO_DEVICE;
+    }
+    CK(cudaSetDevice(device));
+    lpdec_ctx* c = new (std::nothrow) lpdec_ctx();
+    if (!c) return LPDEC_ERR_INVALID_ARG;
+    c->device = device;
+    if (params) c->prm = *params; else lpdec_default_params(&c->prm);
+    c->budget = hbm_budget_bytes;
+    c->sm_count = prop.multiProcessorCount;
+    c->smem_optin = (int)prop.sharedMemPerBlockOptin;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&c->counter, sizeof(int)) != cudaSuccess) {
+        snprintf(g_err, sizeof g_err, "context allocation failed");
+        if (c->stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return LPDEC_ERR_CUDA;
+    }
+    *out = c;
+    return LPDEC_OK;
+}
+
+void lpdec_ctx_destroy(lpdec_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->gscratch);
+    cudaFree(ctx->staging);
+    cudaFree(ctx->counter);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int32_t lpdec_ctx_set_params(lpdec_ctx* ctx, const lpdec_params* params) {
+    if (!ctx || !params) return LPDEC_ERR_INVALID_ARG;
+    if (params->variant != LPDEC_MALP_A && params->variant != LPDEC_MALP_B) return LPDEC_ERR_INVALID_ARG;
+    if (params->precision != LPDEC_FP64 && params->precision != LPDEC_MIXED) return LPDEC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->prm = *params;
+    return LPDEC_OK;
+}
+
+int32_t lpdec_code_create(lpdec_ctx* ctx, int32_t m, int32_t n, const int32_t* row_ptr,
+                          const int32_t* col_idx, lpdec_code** out) {
+    if (!ctx || !out || !row_ptr || m <= 0 || n <= 0 || m > 32767 || n > 32767)
+        return LPDEC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (row_ptr[0] != 0) return LPDEC_ERR_INVALID_ARG;
+    for (int j = 0; j < m; ++j) {
+        int d = row_ptr[j + 1] - row_ptr[j];
+        if (d < 1 || d > 32) return LPDEC_ERR_INVALID_ARG;
+    }
+    const int E = row_ptr[m];
+    if (E > 0 && !col_idx) return LPDEC_ERR_INVALID_ARG;
+    std::vector<int> e_chk(E), vdeg(n + 1, 0);
+    for (int j = 0; j < m; ++j) {
+        for (int e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
+            int i = col_idx[e];
+            if (i < 0 || i >= n) return LPDEC_ERR_INVALID_ARG;
+            if (e > row_ptr[j] && col_idx[e - 1] >= i) return LPDEC_ERR_INVALID_ARG;
+            e_chk[e] = j;
+            vdeg[i + 1]++;
+        }
+    }
+    std::vector<int> v_ptr(n + 1, 0), v_chk(E), v_eidx(E);
+    for (int i = 0; i < n; ++i) v_ptr[i + 1] = v_ptr[i] + vdeg[i + 1];
+    std::vector<int> fill(v_ptr.begin(), v_ptr.end() - 1);
+    for (int j = 0; j < m; ++j)
+        for (int e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
+            int i = col_idx[e];
+            v_chk[fill[i]] = j;
+            v_eidx[fill[i]] = e;
+            fill[i]++;
+        }
+    CK(cudaSetDevice(ctx->device));
+    lpdec_code* c = new (std::nothrow) lpdec_code();
+    if (!c) return LPDEC_ERR_INVALID_ARG;
+    c->ctx = ctx;
+    c->m = m; c->n = n; c->E = E;
+    auto up = [&](int** dst, const int* src, size_t cnt) -> bool {
+        if (cudaMalloc(dst, std::max<size_t>(cnt, 1) * sizeof(int)) != cudaSuccess) return false;
+        return cnt == 0 || cudaMemcpy(*dst, src, cnt * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    bool ok = up(&c->h_ptr, row_ptr, m + 1) && up(&c->h_col, col_idx, E) &&
+              up(&c->e_chk, e_chk.data(), E) && up(&c->v_ptr, v_ptr.data(), n + 1) &&
+              up(&c->v_chk, v_chk.data(), E) && up(&c->v_eidx, v_eidx.data(), E);
+    if (!ok) {
+        snprintf(g_err, sizeof g_err, "code upload failed");
+        lpdec_code_destroy(c);
+        return LPDEC_ERR_CUDA;
+    }
+    *out = c;
+    return LPDEC_OK;
+}
+
+void lpdec_code_destroy(lpdec_code* code) {
+    if (!code) return;
+    if (code->ctx) cudaSetDevice(code->ctx->device);
+    cudaFree(code->h_ptr); cudaFree(code->h_col); cudaFree(code->e_chk);
+    cudaFree(code->v_ptr); cudaFree(code->v_chk); cudaFree(code->v_eidx);
+    delete code;
+}
+
+int32_t lpdec_decode_batch_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                                  const double* d_gamma, double* d_u, uint8_t* d_hard,
+                                  int32_t* d_cert, uint32_t* d_cut_mask, lpdec_stats* d_stats,
+                                  void* stream) {
+    int32_t rc = check_ctx_code(ctx, code);
+    if (rc) return rc;
+    if (nframes < 0 || (nframes > 0 && (!d_gamma || !d_u || !d_hard || !d_cert)))
+        return LPDEC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    return launch_decode(ctx, code, nframes, d_gamma, d_u, d_hard, d_cert, d_cut_mask, d_stats,
+                         (cudaStream_t)stream);
+}
+
+int32_t lpdec_decode_batch(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                           const double* gamma, double* u_out, uint8_t* hard_out,
+                           int32_t* cert_out, uint32_t* cut_mask_out, lpdec_stats* stats) {
+    int32_t rc = check_ctx_code(ctx, code);
+    if (rc) return rc;
+    if (nframes < 0 || (nframes > 0 && (!gamma || !u_out || !hard_out || !cert_out)))
+        return LPDEC_ERR_INVALID_ARG;
+    if (nframes == 0) return LPDEC_OK;
+    for (size_t k = 0; k < (size_t)nframes * code->n; ++k)
+        if (!std::isfinite(gamma[k])) return LPDEC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    const size_t nf = (size_t)nframes, n = code->n, m = code->m;
+    size_t o_g = 0;
+    size_t o_u = align_up(o_g + nf * n * 8, 256);
+    size_t o_h = align_up(o_u + nf * n * 8, 256);
+    size_t o_c = align_up(o_h + nf * n, 256);
+    size_t o_m = align_up(o_c + nf * 4, 256);
+    size_t o_s = align_up(o_m + nf * m * 4, 256);
+    size_t tot = align_up(o_s + nf * sizeof(lpdec_stats), 256);
+    rc = staging(ctx, tot);
+    if (rc) return rc;
+    char* b = ctx->staging;
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(b + o_g, gamma, nf * n * 8, cudaMemcpyHostToDevice, s));
+    rc = launch_decode(ctx, code, nframes, (const double*)(b + o_g), (double*)(b + o_u),
+                       (uint8_t*)(b + o_h), (int32_t*)(b + o_c),
+                       cut_mask_out ? (uint32_t*)(b + o_m) : nullptr,
+                       stats ? (lpdec_stats*)(b + o_s) : nullptr, s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(u_out, b + o_u, nf * n * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hard_out, b + o_h, nf * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(cert_out, b + o_c, nf * 4, cudaMemcpyDeviceToHost, s));
+    if (cut_mask_out) CK(cudaMemcpyAsync(cut_mask_out, b + o_m, nf * m * 4, cudaMemcpyDeviceToHost, s));
+    if (stats) CK(cudaMemcpyAsync(stats, b + o_s, nf * sizeof(lpdec_stats), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return LPDEC_OK;
+}
+
+int32_t lpdec_decode(lpdec_ctx* ctx, const lpdec_code* code, const double* gamma, double* u_out,
+                     uint8_t* hard_out, int32_t* cert_out, uint32_t* cut_mask_out,
+                     lpdec_stats* stats) {
+    return lpdec_decode_batch(ctx, code, 1, gamma, u_out, hard_out, cert_out, cut_mask_out, stats);
+}
+
+int32_t lpdec_cut_search_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                                const double* d_u, const uint8_t* d_active, uint8_t* d_in_lp,
+                                uint32_t* d_mask, int32_t* d_flag, void* stream) {
+    int32_t rc = check_ctx_code(ctx, code);
+    if (rc) return rc;
+    if (nframes < 0 || (nframes > 0 && (!d_u || !d_active || !d_in_lp || !d_mask || !d_flag)))
+        return LPDEC_ERR_INVALID_ARG;
+    if (nframes == 0) return LPDEC_OK;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Launch ln;
+    const bool mixed = ctx->prm.precision == LPDEC_MIXED;
+    rc = mixed ? plan(ctx, code, nframes, k_cut_search<float>, 4, &ln)
+               : plan(ctx, code, nframes, k_cut_search<double>, 8, &ln);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
+    if (mixed)
+        k_cut_search<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+        view_of(code), to_dev(ctx->prm), ln.L, d_u, d_active, d_in_lp, d_mask, d_flag, nframes,
+        ctx->counter, ctx->gscratch);
+    else
+        k_cut_search<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+        view_of(code), to_dev(ctx->prm), ln.L, d_u, d_active, d_in_lp, d_mask, d_flag, nframes,
+        ctx->counter, ctx->gscratch);
+    CK(cudaGetLastError());
+    return LPDEC_OK;
+}
+
+int32_t lpdec_mts_select_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                                const double* d_gamma, const uint8_t* d_in_lp,
+                                const uint32_t* d_mask, const double* d_w, int32_t* d_col,
+                                int32_t* d_row, void* stream) {
+    int32_t rc = check_ctx_code(ctx, code);
+    if (rc) return rc;
+    if (nframes < 0 || (nframes > 0 && (!d_gamma || !d_in_lp || !d_mask || !d_w || !d_col || !d_row)))
+        return LPDEC_ERR_INVALID_ARG;
+    if (nframes == 0) return LPDEC_OK;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Launch ln;
+    const bool mixed = ctx->prm.precision == LPDEC_MIXED;
+    rc = mixed ? plan(ctx, code, nframes, k_mts_select<float>, 4, &ln)
+               : plan(ctx, code, nframes, k_mts_select<double>, 8, &ln);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
+    if (mixed)
+        k_mts_select<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_w, d_col, d_row,
+        nframes, ctx->counter, ctx->gscratch);
+    else
+        k_mts_select<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_w, d_col, d_row,
+        nframes, ctx->counter, ctx->gscratch);
+    CK(cudaGetLastError());
+    return LPDEC_OK;
+}
+
+int32_t lpdec_pcg_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                         const double* d_gamma, const uint8_t* d_in_lp, const uint32_t* d_mask,
+                         const double* d_d2, const double* d_w, double* d_dy, int32_t* d_iters,
+                         void* stream) {
+    int32_t rc = check_ctx_code(ctx, code);
+    if (rc) return rc;
+    if (nframes < 0 || (nframes > 0 && (!d_gamma || !d_in_lp || !d_mask || !d_d2 || !d_w || !d_dy || !d_iters)))
+        return LPDEC_ERR_INVALID_ARG;
+    if (nframes == 0) return LPDEC_OK;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Launch ln;
+    const bool mixed = ctx->prm.precision == LPDEC_MIXED;
+    rc = mixed ? plan(ctx, code, nframes, k_pcg<float>, 4, &ln)
+               : plan(ctx, code, nframes, k_pcg<double>, 8, &ln);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
+    if (mixed)
+        k_pcg<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_dy,
+        d_iters, nframes, ctx->counter, ctx->gscratch);
+    else
+        k_pcg<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_dy,
+        d_iters, nframes, ctx->counter, ctx->gscratch);
+    CK(cudaGetLastError());
+    return LPDEC_OK;
+}
+
+int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                                    const double* d_gamma, const uint8_t* d_in_lp,
+                                    const uint32_t* d_mask, double* d_x, lpdec_stats* d_stats,
+                                    double* d_trace, int32_t max_trace, void* stream);
+
+int32_t lpdec_lp_solve_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                              const double* d_gamma, const uint8_t* d_in_lp,
+                              const uint32_t* d_mask, double* d_x, lpdec_stats* d_stats,
+                              void* stream) {
+    return lpdec_lp_solve_trace_device(ctx, code, nframes, d_gamma, d_in_lp, d_mask, d_x,
+                                       d_stats, nullptr, 0, stream);
+}
+
+int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                                    const double* d_gamma, const uint8_t* d_in_lp,
+                                    const uint32_t* d_mask, double* d_x, lpdec_stats* d_stats,
+                                    double* d_trace, int32_t max_trace, void* stream) {
+    int32_t rc = check_ctx_code(ctx, code);
+    if (rc) return rc;
+    if (nframes < 0 || (nframes > 0 && (!d_gamma || !d_in_lp || !d_mask || !d_x || !d_stats)))
+        return LPDEC_ERR_INVALID_ARG;
+    if (nframes == 0) return LPDEC_OK;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Launch ln;
+    const bool mixed = ctx->prm.precision == LPDEC_MIXED;
+    rc = mixed ? plan(ctx, code, nframes, k_lp_solve<float>, 4, &ln)
+               : plan(ctx, code, nframes, k_lp_solve<double>, 8, &ln);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
+    if (mixed)
+        k_lp_solve<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_x, d_stats, nframes,
+        ctx->counter, ctx->gscratch, d_trace, d_trace ? max_trace : 0);
+    else
+        k_lp_solve<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_x, d_stats, nframes,
+        ctx->counter, ctx->gscratch, d_trace, d_trace ? max_trace : 0);
+    CK(cudaGetLastError());
+    return LPDEC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,306 @@
+"""Python binding of the decoder's C ABI (include/lpdec.h).
+
+Functions carry the C names and only marshal arguments: numpy arrays for
+host pointers, torch CUDA tensors (or integer addresses) for device
+pointers, a torch stream (or integer handle) for ``stream``. Every
+computation runs in the CUDA kernels of liblpdec.so; importing this module
+raises if the library is missing, and there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LPDEC_OK = 0
+LPDEC_ERR_INVALID_ARG = -1
+LPDEC_ERR_OUT_OF_BUDGET = -2
+LPDEC_ERR_NOT_CONVERGED = -3
+LPDEC_ERR_TIMEOUT = -4
+LPDEC_ERR_PENDING = -5
+LPDEC_ERR_CUDA = -6
+LPDEC_ERR_NO_DEVICE = -7
+LPDEC_MALP_A = 0
+LPDEC_MALP_B = 1
+LPDEC_FP64 = 0
+LPDEC_MIXED = 1
+
+
+class lpdec_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("sigma", "eta", "tol_gap", "tol_feas", "tol_pcg", "tau_act", "tau_cut", "tau_int",
+                 "pcg_gap_factor", "tol_inner", "tol_feas_loose")] + \
+               [(k, ctypes.c_int32) for k in
+                ("max_alp", "max_ipm", "max_pcg", "variant", "precision",
+                 "threads_per_block", "smem_budget", "reserved")]
+
+
+class lpdec_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in
+                ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total", "lp_rows_final",
+                 "vertex_failures", "max_levels", "reserved")] + [("objective", ctypes.c_double)]
+
+
+STATS_DTYPE = np.dtype([(k, np.int32) for k in
+                        ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total",
+                         "lp_rows_final", "vertex_failures", "max_levels", "reserved")] +
+                       [("objective", np.float64)])
+assert STATS_DTYPE.itemsize == ctypes.sizeof(lpdec_stats)
+
+
+class LpdecError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {error_string(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"decoder library not built ({path}); run "
+                           "paper_0902_0657_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32 = ctypes.c_int32
+    lib.lpdec_default_params.argtypes = [ctypes.POINTER(lpdec_params)]
+    lib.lpdec_default_params.restype = None
+    lib.lpdec_error_string.argtypes = [i32]
+    lib.lpdec_error_string.restype = ctypes.c_char_p
+    lib.lpdec_workspace_bytes.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t),
+                                          ctypes.POINTER(ctypes.c_size_t)]
+    lib.lpdec_workspace_bytes.restype = i32
+    lib.lpdec_ctx_create.argtypes = [i32, ctypes.POINTER(lpdec_params), ctypes.c_size_t,
+                                     ctypes.POINTER(P)]
+    lib.lpdec_ctx_destroy.argtypes = [P]
+    lib.lpdec_ctx_destroy.restype = None
+    lib.lpdec_ctx_set_params.argtypes = [P, ctypes.POINTER(lpdec_params)]
+    lib.lpdec_code_create.argtypes = [P, i32, i32, P, P, ctypes.POINTER(P)]
+    lib.lpdec_code_destroy.argtypes = [P]
+    lib.lpdec_code_destroy.restype = None
+    lib.lpdec_decode.argtypes = [P, P, P, P, P, P, P, P]
+    lib.lpdec_decode_batch.argtypes = [P, P, i32, P, P, P, P, P, P]
+    lib.lpdec_decode_batch_device.argtypes = [P, P, i32, P, P, P, P, P, P, P]
+    lib.lpdec_cut_search_device.argtypes = [P, P, i32, P, P, P, P, P, P]
+    lib.lpdec_mts_select_device.argtypes = [P, P, i32, P, P, P, P, P, P, P]
+    lib.lpdec_pcg_device.argtypes = [P, P, i32, P, P, P, P, P, P, P, P]
+    lib.lpdec_lp_solve_device.argtypes = [P, P, i32, P, P, P, P, P, P]
+    lib.lpdec_lp_solve_trace_device.argtypes = [P, P, i32, P, P, P, P, P, P, i32, P]
+    for name in ("lpdec_ctx_create", "lpdec_ctx_set_params", "lpdec_code_create",
+                 "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_batch_device",
+                 "lpdec_cut_search_device", "lpdec_mts_select_device", "lpdec_pcg_device",
+                 "lpdec_lp_solve_device", "lpdec_lp_solve_trace_device"):
+        getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def library():
+    """The loaded ctypes library (loads it on first use)."""
+    return _load()
+
+
+def _check(rc: int, what: str):
+    if rc != LPDEC_OK:
+        raise LpdecError(rc, what)
+
+
+def _hptr(a, dtype):
+    """Host pointer of a C-contiguous numpy array of the given dtype."""
+    if a is None:
+        return None
+    if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous):
+        raise TypeError(f"expected a C-contiguous numpy array of {dtype}")
+    return a.ctypes.data
+
+
+def _dptr(t):
+    """Device pointer: a torch CUDA tensor (contiguous) or an integer."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not (t.is_cuda and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# C entry points
+# ---------------------------------------------------------------------------
+
+def lpdec_default_params() -> lpdec_params:
+    p = lpdec_params()
+    _load().lpdec_default_params(ctypes.byref(p))
+    return p
+
+
+def error_string(code: int) -> str:
+    return _load().lpdec_error_string(code).decode()
+
+
+lpdec_error_string = error_string
+
+
+def lpdec_workspace_bytes(m: int, n: int, E: int, precision: int = LPDEC_FP64,
+                          smem_budget: int = 0):
+    """(rc, shared bytes per CTA, global scratch bytes per frame)."""
+    sm = ctypes.c_size_t()
+    gl = ctypes.c_size_t()
+    rc = _load().lpdec_workspace_bytes(m, n, E, precision, smem_budget, ctypes.byref(sm),
+                                       ctypes.byref(gl))
+    return rc, sm.value, gl.value
+
+
+def lpdec_ctx_create(device: int = 0, params: lpdec_params | None = None,
+                     hbm_budget_bytes: int = 0) -> int:
+    out = ctypes.c_void_p()
+    rc = _load().lpdec_ctx_create(device, ctypes.byref(params) if params is not None else None,
+                                  hbm_budget_bytes, ctypes.byref(out))
+    _check(rc, "lpdec_ctx_create")
+    return out.value
+
+
+def lpdec_ctx_destroy(ctx: int) -> None:
+    _load().lpdec_ctx_destroy(ctx)
+
+
+def lpdec_ctx_set_params(ctx: int, params: lpdec_params) -> None:
+    _check(_load().lpdec_ctx_set_params(ctx, ctypes.byref(params)), "lpdec_ctx_set_params")
+
+
+def lpdec_code_create(ctx: int, m: int, n: int, row_ptr: np.ndarray, col_idx: np.ndarray) -> int:
+    out = ctypes.c_void_p()
+    rc = _load().lpdec_code_create(ctx, m, n, _hptr(row_ptr, np.int32), _hptr(col_idx, np.int32),
+                                   ctypes.byref(out))
+    _check(rc, "lpdec_code_create")
+    return out.value
+
+
+def lpdec_code_destroy(code: int) -> None:
+    _load().lpdec_code_destroy(code)
+
+
+def lpdec_decode(ctx, code, gamma, u_out, hard_out, cert_out, cut_mask_out=None, stats=None) -> int:
+    return _load().lpdec_decode(ctx, code, _hptr(gamma, np.float64), _hptr(u_out, np.float64),
+                                _hptr(hard_out, np.uint8), _hptr(cert_out, np.int32),
+                                _hptr(cut_mask_out, np.uint32), _hptr(stats, STATS_DTYPE))
+
+
+def lpdec_decode_batch(ctx, code, nframes, gamma, u_out, hard_out, cert_out,
+                       cut_mask_out=None, stats=None) -> int:
+    return _load().lpdec_decode_batch(ctx, code, nframes, _hptr(gamma, np.float64),
+                                      _hptr(u_out, np.float64), _hptr(hard_out, np.uint8),
+                                      _hptr(cert_out, np.int32), _hptr(cut_mask_out, np.uint32),
+                                      _hptr(stats, STATS_DTYPE))
+
+
+def lpdec_decode_batch_device(ctx, code, nframes, d_gamma, d_u, d_hard, d_cert,
+                              d_cut_mask=None, d_stats=None, stream=None) -> int:
+    return _load().lpdec_decode_batch_device(ctx, code, nframes, _dptr(d_gamma), _dptr(d_u),
+                                             _dptr(d_hard), _dptr(d_cert), _dptr(d_cut_mask),
+                                             _dptr(d_stats), _stream(stream))
+
+
+def lpdec_cut_search_device(ctx, code, nframes, d_u, d_active, d_in_lp, d_mask, d_flag,
+                            stream=None) -> int:
+    return _load().lpdec_cut_search_device(ctx, code, nframes, _dptr(d_u), _dptr(d_active),
+                                           _dptr(d_in_lp), _dptr(d_mask), _dptr(d_flag),
+                                           _stream(stream))
+
+
+def lpdec_mts_select_device(ctx, code, nframes, d_gamma, d_in_lp, d_mask, d_w, d_col, d_row,
+                            stream=None) -> int:
+    return _load().lpdec_mts_select_device(ctx, code, nframes, _dptr(d_gamma), _dptr(d_in_lp),
+                                           _dptr(d_mask), _dptr(d_w), _dptr(d_col), _dptr(d_row),
+                                           _stream(stream))
+
+
+def lpdec_pcg_device(ctx, code, nframes, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_dy, d_iters,
+                     stream=None) -> int:
+    return _load().lpdec_pcg_device(ctx, code, nframes, _dptr(d_gamma), _dptr(d_in_lp),
+                                    _dptr(d_mask), _dptr(d_d2), _dptr(d_w), _dptr(d_dy),
+                                    _dptr(d_iters), _stream(stream))
+
+
+def lpdec_lp_solve_device(ctx, code, nframes, d_gamma, d_in_lp, d_mask, d_x, d_stats,
+                          stream=None) -> int:
+    return _load().lpdec_lp_solve_device(ctx, code, nframes, _dptr(d_gamma), _dptr(d_in_lp),
+                                         _dptr(d_mask), _dptr(d_x), _dptr(d_stats),
+                                         _stream(stream))
+
+
+def lpdec_lp_solve_trace_device(ctx, code, nframes, d_gamma, d_in_lp, d_mask, d_x, d_stats,
+                                d_trace, max_trace, stream=None) -> int:
+    return _load().lpdec_lp_solve_trace_device(ctx, code, nframes, _dptr(d_gamma), _dptr(d_in_lp),
+                                               _dptr(d_mask), _dptr(d_x), _dptr(d_stats),
+                                               _dptr(d_trace), max_trace, _stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# Convenience owner of a context + code (still only marshalling)
+# ---------------------------------------------------------------------------
+
+class Decoder:
+    """Owns one context and one code; frees both on close()."""
+
+    def __init__(self, code, device: int = 0, params: lpdec_params | None = None,
+                 hbm_budget_bytes: int = 0):
+        self.n, self.m = int(code.n), int(code.m)
+        self.params = params if params is not None else lpdec_default_params()
+        self.ctx = lpdec_ctx_create(device, self.params, hbm_budget_bytes)
+        try:
+            self.code = lpdec_code_create(self.ctx, self.m, self.n,
+                                          np.ascontiguousarray(code.row_ptr, dtype=np.int32),
+                                          np.ascontiguousarray(code.col_idx, dtype=np.int32))
+        except Exception:
+            lpdec_ctx_destroy(self.ctx)
+            raise
+
+    def set_params(self, params: lpdec_params):
+        self.params = params
+        lpdec_ctx_set_params(self.ctx, params)
+
+    def decode_batch(self, gamma: np.ndarray):
+        """Host-pointer batch decode. Returns (u, hard, cert, masks, stats)."""
+        gamma = np.ascontiguousarray(gamma, dtype=np.float64).reshape(-1, self.n)
+        nf = gamma.shape[0]
+        u = np.empty((nf, self.n), np.float64)
+        hard = np.empty((nf, self.n), np.uint8)
+        cert = np.empty(nf, np.int32)
+        masks = np.empty((nf, self.m), np.uint32)
+        stats = np.empty(nf, STATS_DTYPE)
+        _check(lpdec_decode_batch(self.ctx, self.code, nf, gamma, u, hard, cert, masks, stats),
+               "lpdec_decode_batch")
+        return u, hard, cert, masks, stats
+
+    def close(self):
+        if self.code:
+            lpdec_code_destroy(self.code)
+            self.code = None
+        if self.ctx:
+            lpdec_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
