@@ -77,6 +77,10 @@ extern "C" {
  *   tol_feas_loose = 1e-6  the IPM also stops when the gap is below tol_gap and
  *                     both infeasibilities are below this (limited accuracy of
  *                     the Newton solves near the optimum)
+ *   tol_cert = 1e-6   below this gap, whenever the partition x_i > z_i is the
+ *                     same as one iteration earlier, the decoder tries to
+ *                     certify the optimal vertex (primal and dual feasible,
+ *                     complementary) and stops the IPM if it succeeds
  *   tau_act  = 1e-9   an inequality is active iff its slack <= tau_act
  *   tau_cut  = 1e-9   a check is violated iff Eq. 6's left side < 1 - tau_cut
  *   tau_int  = 1e-9   u is integral iff max |u_i - round(u_i)| <= tau_int
@@ -85,13 +89,15 @@ extern "C" {
  *   variant = LPDEC_MALP_A, precision = LPDEC_FP64
  * The decisions are taken on the LP's optimal vertex, recovered from the
  * final interior-point iterate through its strictly complementary
- * partition (basic iff x_i > z_i, Section VI-A).
+ * partition (basic iff x_i > z_i, Section VI-A) and certified optimal by a
+ * primal-dual feasible, complementary pair.
  */
 typedef struct lpdec_params {
     double sigma, eta, tol_gap, tol_feas, tol_pcg, tau_act, tau_cut, tau_int;
     double pcg_gap_factor;  /* Newton solve tolerance = max(tol_pcg, min(1e-3, f * gap)) */
     double tol_inner;       /* relative tolerance of one FP32 PCG round (LPDEC_MIXED) */
     double tol_feas_loose;  /* infeasibility accepted once the gap is below tol_gap */
+    double tol_cert;        /* gap below which the optimality certificate is tried */
     int32_t max_alp, max_ipm, max_pcg, variant, precision;
     int32_t threads_per_block;  /* 0 = library choice */
     int32_t smem_budget;        /* bytes of shared memory per CTA, 0 = library choice */
@@ -107,7 +113,7 @@ typedef struct lpdec_stats {
     int32_t lp_rows_final;    /* p of the last LP (parity inequalities) */
     int32_t vertex_failures;  /* LPs whose optimal-vertex recovery was rejected */
     int32_t max_levels;       /* deepest triangular-solve level schedule seen */
-    int32_t reserved;
+    int32_t pcg_iters_fp64;   /* PCG iterations run in FP64 (all of them in LPDEC_FP64) */
     double  objective;        /* gamma'u */
 } lpdec_stats;
 

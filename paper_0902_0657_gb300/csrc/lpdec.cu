@@ -40,11 +40,13 @@ __device__ __forceinline__ int next_frame(Blk& B, int* counter, int* slot) {
     __shared__ KernelShared ks;                                                 \
     Blk B{(int)threadIdx.x, (int)blockDim.x, (int)(threadIdx.x & 31),          \
           (int)(threadIdx.x >> 5), (int)(blockDim.x >> 5), ks.red, 0};          \
-    WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.gbytes, C.n, C.m, (int)L.q2);
+    WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.gbytes, C0.n, C0.m,      \
+                         (int)L.q2);                                            \
+    const CodeView C = bind_code<T>(C0, W);
 
 template <typename T>
 __global__ void __launch_bounds__(512)
-k_decode(CodeView C, DevParams P, Layout L, const double* __restrict__ gamma,
+k_decode(CodeView C0, DevParams P, Layout L, const double* __restrict__ gamma,
          double* u, uint8_t* hard, int32_t* cert, uint32_t* mask, lpdec_stats* stats,
          int nframes, int* counter, char* gscratch) {
     KERNEL_PROLOGUE
@@ -78,7 +80,7 @@ __device__ inline void load_lp_state(Blk& B, const CodeView& C, WS<T>& W, const 
 
 template <typename T>
 __global__ void __launch_bounds__(512)
-k_cut_search(CodeView C, DevParams P, Layout L, const double* u, const uint8_t* active,
+k_cut_search(CodeView C0, DevParams P, Layout L, const double* u, const uint8_t* active,
              uint8_t* in_lp, uint32_t* mask, int32_t* flag, int nframes, int* counter,
              char* gscratch) {
     KERNEL_PROLOGUE
@@ -107,7 +109,7 @@ k_cut_search(CodeView C, DevParams P, Layout L, const double* u, const uint8_t* 
 
 template <typename T>
 __global__ void __launch_bounds__(512)
-k_mts_select(CodeView C, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
+k_mts_select(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
              const uint32_t* mask, const double* wts, int32_t* col, int32_t* row,
              int nframes, int* counter, char* gscratch) {
     KERNEL_PROLOGUE
@@ -129,7 +131,7 @@ k_mts_select(CodeView C, DevParams P, Layout L, const double* gamma, const uint8
 
 template <typename T>
 __global__ void __launch_bounds__(512)
-k_pcg(CodeView C, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
+k_pcg(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
       const uint32_t* mask, const double* d2, const double* wv, double* dy, int32_t* iters,
       int nframes, int* counter, char* gscratch) {
     KERNEL_PROLOGUE
@@ -148,7 +150,8 @@ k_pcg(CodeView C, DevParams P, Layout L, const double* gamma, const uint8_t* in_
         for (int i = B.tid; i < F.q; i += B.nt) W.d2t[i] = (T)W.d2[i];
         for (int r = B.tid; r < F.p; r += B.nt) W.invd2p[r] = (T)(1.0 / W.d2[W.pivcol[r]]);
         __syncthreads();
-        NewtonOut no = newton_solve<T>(B, C, W, F, Lv, P, P.tol_pcg, P.max_pcg);
+        bool force64 = false;
+        NewtonOut no = newton_solve<T>(B, C, W, F, Lv, P, P.tol_pcg, P.max_pcg, force64);
         for (int r = B.tid; r < C.m; r += B.nt) dy[(size_t)f * C.m + r] = r < F.p ? W.dy[r] : 0.0;
         if (B.tid == 0) iters[f] = no.iters;
         __syncthreads();
@@ -157,7 +160,7 @@ k_pcg(CodeView C, DevParams P, Layout L, const double* gamma, const uint8_t* in_
 
 template <typename T>
 __global__ void __launch_bounds__(512)
-k_lp_solve(CodeView C, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
+k_lp_solve(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
            const uint32_t* mask, double* xo, lpdec_stats* stats, int nframes, int* counter,
            char* gscratch, double* trace, int max_trace) {
     KERNEL_PROLOGUE
@@ -174,11 +177,13 @@ k_lp_solve(CodeView C, DevParams P, Layout L, const double* gamma, const uint8_t
             IpmOut io = ipm_solve<T>(B, C, W, F, P, g, (int)L.q2,
                                      trace ? trace + (size_t)f * 8 * max_trace : nullptr,
                                      max_trace);
-            st.vertex_failures = vertex_recover<T>(B, C, W, F, g);
+            int ok = io.certified || certify<T>(B, C, W, F, g);
+            if (!ok) st.vertex_failures = vertex_recover<T>(B, C, W, F, g);
             st.ipm_iters_total = io.iters;
             st.pcg_iters_total = io.pcg_iters;
+            st.pcg_iters_fp64 = io.pcg_iters64;
             st.max_levels = io.max_levels;
-            st.status = io.converged ? LPDEC_OK : LPDEC_ERR_NOT_CONVERGED;
+            st.status = (io.converged || ok) ? LPDEC_OK : LPDEC_ERR_NOT_CONVERGED;
         } else {
             for (int i = B.tid; i < C.n; i += B.nt) W.x[i] = 0.0;
             __syncthreads();
@@ -242,6 +247,7 @@ DevParams to_dev(const lpdec_params& p) {
     d.tol_pcg = p.tol_pcg; d.tau_act = p.tau_act; d.tau_cut = p.tau_cut; d.tau_int = p.tau_int;
     d.pcg_gap_factor = p.pcg_gap_factor; d.tol_inner = p.tol_inner;
     d.tol_feas_loose = p.tol_feas_loose;
+    d.tol_cert = p.tol_cert;
     d.max_alp = p.max_alp; d.max_ipm = p.max_ipm; d.max_pcg = p.max_pcg;
     d.variant = p.variant; d.precision = p.precision;
     return d;
@@ -297,10 +303,14 @@ Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes) {
         {S_PIVCOL, H * m, 0}, {S_ROWCHK, H * m, 0}, {S_CHKROW, H * m, 0}, {S_PSGN, (size_t)m, 0},
         {S_LBROWS, H * m, 0}, {S_LFROWS, H * m, 0}, {S_LB, H * m, 0}, {S_LF, H * m, 0},
         {S_SELROW, H * m, 0}, {S_DEG, q, 0}, {S_FLAGS, (size_t)m, 0}, {S_MASK, I * m, 0},
-        {S_FLIP, I * ((n + 31) / 32), 0},
+        {S_FLIP, I * ((n + 31) / 32), 0}, {S_HPTR, I * (m + 1), 0}, {S_VPTR, I * (n + 1), 0},
+        {S_BPTR, I * (m + 1), 0}, {S_FPTR, I * (m + 1), 0}, {S_BDEP, H * E, 0}, {S_FDEP, H * E, 0},
         {G_X, D * q, 2}, {G_Z, D * q, 2}, {G_RC, D * q, 2}, {G_D2, D * q, 2}, {G_Y, D * m, 2},
         {G_B, D * m, 2}, {G_W, D * m, 2}, {G_DY, D * m, 2}, {G_R64, D * m, 2}, {G_U, D * n, 2},
         {G_T64, D * n, 2}, {G_BASIC, q, 2},
+        {G_VX, D * q, 2}, {G_V1, D * q, 2}, {G_V2, D * q, 2}, {G_V3, D * q, 2}, {G_V4, D * q, 2},
+        {G_VR1, D * m, 2}, {G_VR2, D * m, 2},
+        {G_P64, real_bytes < 8 ? D * vec_elems(n, m) : 16, 2},
     };
     Layout L{};
     size_t s = 0, g = 0;
@@ -428,6 +438,7 @@ void lpdec_default_params(lpdec_params* p) {
     p->pcg_gap_factor = 0.01;
     p->tol_inner = 1e-5;
     p->tol_feas_loose = 1e-6;
+    p->tol_cert = 1e-6;
     p->max_alp = 200;
     p->max_ipm = 200;
     p->max_pcg = 2000;

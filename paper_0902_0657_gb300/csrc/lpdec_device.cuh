@@ -39,7 +39,7 @@ struct CodeView {
 
 struct DevParams {
     double sigma, eta, tol_gap, tol_feas, tol_pcg, tau_act, tau_cut, tau_int;
-    double pcg_gap_factor, tol_inner, tol_feas_loose;
+    double pcg_gap_factor, tol_inner, tol_feas_loose, tol_cert;
     int max_alp, max_ipm, max_pcg, variant, precision;
 };
 
@@ -50,12 +50,19 @@ enum Arr {
     // hot arrays (shared memory)
     S_ROWENT, S_COLENT, S_ROWCHK, S_CHKROW, S_PIVCOL, S_PIVROW, S_PSGN,
     S_LB, S_LF, S_LBPTR, S_LFPTR, S_CUR, S_LBROWS, S_LFROWS, S_SELROW,
-    S_DEG, S_BITMAP, S_FLAGS, S_MASK, S_FLIP,
+    S_DEG, S_BITMAP, S_FLAGS, S_MASK, S_FLIP, S_HPTR, S_VPTR,
+    S_BPTR, S_BDEP, S_FPTR, S_FDEP,   // dependency lists of the two triangular solves
     S_VEC,      // PCG vectors of type T: xs, r, z, h, l (m each), t (n), d2t (n+m), invd2p (m);
                 // during the MTS selection the same bytes hold the u64 sort keys
                 // [q2] followed by rank [q] and sorted [q] (uint16)
     // FP64 interior-point state (global scratch)
     G_X, G_Z, G_RC, G_D2, G_Y, G_B, G_W, G_DY, G_R64, G_U, G_T64, G_BASIC,
+    // optimality certificate scratch: vertex and CG vectors over columns
+    // (4 x n+m) and rows (2 x m)
+    G_VX, G_V1, G_V2, G_V3, G_V4, G_VR1, G_VR2,
+    // FP64 PCG vectors for the fallback rounds of the mixed mode (layout of
+    // S_VEC with T = double)
+    G_P64,
     A_COUNT
 };
 
@@ -79,10 +86,14 @@ struct WS {
     uint16_t *rowent, *colent, *rowchk, *chkrow, *pivcol, *pivrow, *lb, *lf, *lbrows, *lfrows;
     uint16_t *selrow, *rank, *sorted;
     uint32_t *lbptr, *lfptr, *cur, *bitmap, *mask, *flip;
+    int *hptr, *vptr;   // shared copies of the code's CSR / CSC row pointers
+    uint32_t *bptr, *fptr;
+    uint16_t *bdep, *fdep;   // packed (row | kNeg): rows whose solved values row r needs
     uint8_t *psgn, *deg, *flags, *basic;
     T *xs, *r, *z, *h, *l, *t, *d2t, *invd2p;
     unsigned long long* skey;   // aliases the PCG vectors
     double *x, *zz, *rc, *d2, *y, *b, *w, *dy, *r64, *u, *t64;
+    double *vx, *v1, *v2, *v3, *v4, *vr1, *vr2, *p64;
 };
 
 __device__ __forceinline__ char* ws_ptr(const Layout& L, int a, char* smem, char* gws) {
@@ -104,6 +115,9 @@ __device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws, int n, i
     P_(uint8_t, deg, S_DEG);
     P_(uint32_t, bitmap, S_BITMAP); P_(uint8_t, flags, S_FLAGS); P_(uint32_t, mask, S_MASK);
     P_(uint32_t, flip, S_FLIP);
+    P_(int, hptr, S_HPTR); P_(int, vptr, S_VPTR);
+    P_(uint32_t, bptr, S_BPTR); P_(uint32_t, fptr, S_FPTR);
+    P_(uint16_t, bdep, S_BDEP); P_(uint16_t, fdep, S_FDEP);
     T* v = reinterpret_cast<T*>(ws_ptr(L, S_VEC, smem, gws));
     w.skey = reinterpret_cast<unsigned long long*>(v);
     w.rank = reinterpret_cast<uint16_t*>(w.skey + q2);
@@ -114,8 +128,49 @@ __device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws, int n, i
     P_(double, y, G_Y); P_(double, b, G_B); P_(double, w, G_W); P_(double, dy, G_DY);
     P_(double, r64, G_R64); P_(double, u, G_U); P_(double, t64, G_T64);
     P_(uint8_t, basic, G_BASIC);
+    P_(double, vx, G_VX); P_(double, v1, G_V1); P_(double, v2, G_V2); P_(double, v3, G_V3);
+    P_(double, v4, G_V4); P_(double, vr1, G_VR1); P_(double, vr2, G_VR2);
+    P_(double, p64, G_P64);
 #undef P_
     return w;
+}
+
+// A view with FP64 PCG vectors (in global scratch) and the same LP
+// structure, for the FP64 fallback rounds of the mixed mode. d2t is the FP64
+// D^2 itself.
+template <typename T>
+__device__ inline WS<double> fp64_view(const WS<T>& W, int n, int m) {
+    WS<double> v;
+    v.rowent = W.rowent; v.colent = W.colent; v.rowchk = W.rowchk; v.chkrow = W.chkrow;
+    v.pivcol = W.pivcol; v.pivrow = W.pivrow; v.lb = W.lb; v.lf = W.lf; v.lbrows = W.lbrows;
+    v.lfrows = W.lfrows; v.selrow = W.selrow; v.rank = W.rank; v.sorted = W.sorted;
+    v.lbptr = W.lbptr; v.lfptr = W.lfptr; v.cur = W.cur; v.bitmap = W.bitmap; v.mask = W.mask;
+    v.flip = W.flip; v.psgn = W.psgn; v.deg = W.deg; v.flags = W.flags; v.basic = W.basic;
+    v.hptr = W.hptr; v.vptr = W.vptr;
+    v.bptr = W.bptr; v.fptr = W.fptr; v.bdep = W.bdep; v.fdep = W.fdep;
+    double* q = W.p64;
+    v.xs = q; q += m; v.r = q; q += m; v.z = q; q += m; v.h = q; q += m; v.l = q; q += m;
+    v.t = q; q += n; v.invd2p = q;
+    v.d2t = W.d2;
+    v.skey = nullptr;
+    v.x = W.x; v.zz = W.zz; v.rc = W.rc; v.d2 = W.d2; v.y = W.y; v.b = W.b; v.w = W.w;
+    v.dy = W.dy; v.r64 = W.r64; v.u = W.u; v.t64 = W.t64;
+    v.vx = W.vx; v.v1 = W.v1; v.v2 = W.v2; v.v3 = W.v3; v.v4 = W.v4; v.vr1 = W.vr1;
+    v.vr2 = W.vr2; v.p64 = W.p64;
+    return v;
+}
+
+// Copies the code's row and column pointers into the workspace (shared
+// memory) and returns a view of the code that reads them from there.
+template <typename T>
+__device__ inline CodeView bind_code(const CodeView& C, WS<T>& W) {
+    for (int k = threadIdx.x; k <= C.m; k += blockDim.x) W.hptr[k] = C.h_ptr[k];
+    for (int k = threadIdx.x; k <= C.n; k += blockDim.x) W.vptr[k] = C.v_ptr[k];
+    __syncthreads();
+    CodeView v = C;
+    v.h_ptr = W.hptr;
+    v.v_ptr = W.vptr;
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -368,6 +423,54 @@ __device__ inline void bitonic_sort(Blk& B, unsigned long long* key, int n2) {
 
 struct Levels { int nb, nf; };
 
+// Dependency lists of the two triangular solves, in CSR form over the LP
+// rows: row r's back-substitution step needs the solved values of the rows
+// pivoting the other selected columns of row r; its forward step needs the
+// other rows of its own pivot column. Each entry is (row | kNeg when the
+// coefficient is -1).
+template <typename T>
+__device__ inline void build_deps(Blk& B, const CodeView& C, WS<T>& W, const Frame& F) {
+    const int n = C.n, p = F.p;
+    int* sh = reinterpret_cast<int*>(B.red);   // scan scratch (33 ints) in the reduction buffer
+    const int per = (p + B.nt - 1) / B.nt;
+    const int r0 = B.tid * per, r1 = min(p, r0 + per);
+    int cb = 0, cf = 0;
+    for (int r = r0; r < r1; ++r) {
+        const int i0 = W.pivcol[r], j = W.rowchk[r];
+        for (int e = C.h_ptr[j]; e < C.h_ptr[j + 1]; ++e) {
+            int i2 = W.rowent[e] & kIdx;
+            cb += (i2 != i0 && W.pivrow[i2] != kNone);
+        }
+        if (i0 < n)
+            for (int k = C.v_ptr[i0]; k < C.v_ptr[i0 + 1]; ++k) {
+                uint16_t ent = W.colent[k];
+                cf += (ent != kNone && (ent & kIdx) != r);
+            }
+    }
+    int tb, tf;
+    int ob = bscan_excl(B, cb, &tb, sh);
+    int of = bscan_excl(B, cf, &tf, sh);
+    for (int r = r0; r < r1; ++r) {
+        const int i0 = W.pivcol[r], j = W.rowchk[r];
+        W.bptr[r] = ob;
+        W.fptr[r] = of;
+        for (int e = C.h_ptr[j]; e < C.h_ptr[j + 1]; ++e) {
+            uint16_t ent = W.rowent[e];
+            int i2 = ent & kIdx;
+            if (i2 == i0) continue;
+            uint16_t pr = W.pivrow[i2];
+            if (pr != kNone) W.bdep[ob++] = (uint16_t)(pr | (ent & kNeg));
+        }
+        if (i0 < n)
+            for (int k = C.v_ptr[i0]; k < C.v_ptr[i0 + 1]; ++k) {
+                uint16_t ent = W.colent[k];
+                if (ent != kNone && (ent & kIdx) != r) W.fdep[of++] = ent;
+            }
+    }
+    if (B.tid == 0) { W.bptr[p] = tb; W.fptr[p] = tf; }
+    __syncthreads();
+}
+
 template <typename T>
 __device__ inline Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                     const double* wt, int q2) {
@@ -518,6 +621,7 @@ __device__ inline Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const F
     __syncthreads();
     for (int r = B.tid; r < p; r += B.nt) W.lfrows[atomicAdd(&W.cur[W.lf[r]], 1u)] = (uint16_t)r;
     __syncthreads();
+    build_deps<T>(B, C, W, F);
     return L;
 }
 
@@ -532,62 +636,90 @@ __device__ inline void selection_order(Blk& B, WS<T>& W, const Frame& F, int32_t
     }
 }
 
-// ---------------------------------------------------------------------------
-// a5: M-solve (Section V): A_M f1 = r by back substitution over the upper-
-// triangular order of Algorithm 7, f2 = f1 / d_M^2, then A_M' z = f2 by
-// forward substitution. Both run level by level. out[r] first holds the
-// value of r's pivot column in f1, then z_r. If alpha != 0, the PCG update
-// r -= alpha l, xs += alpha h of each row is fused into its back-
-// substitution step.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ inline void msolve(Blk& B, const CodeView& C, WS<T>& W, const Levels& L,
-                              T* rvec, T* out, T alpha) {
-    for (int lev = 1; lev <= L.nb; ++lev) {
-        const int i1 = W.lbptr[lev + 1];
-        for (int idx = W.lbptr[lev] + B.tid; idx < i1; idx += B.nt) {
-            int r = W.lbrows[idx];
+// One row of a triangular solve, reduced by a group of G lanes (G a power
+// of two <= 32, g = lane index inside the group): the group sums its share
+// of the row's dependencies and the leader (g == 0) finishes the row. Back:
+// out[r] = +-(r_r - sum); forward: out[r] = +-(out[r] / d_piv - sum). All 32
+// lanes of the warp call this (r < 0 marks an idle group).
+template <typename T, bool kBack>
+__device__ __forceinline__ void solve_row(WS<T>& W, int r, int g, int G, T* rvec, T* out,
+                                          T alpha) {
+    T acc = T(0);
+    if (r >= 0) {
+        const uint32_t* ptr = kBack ? W.bptr : W.fptr;
+        const uint16_t* dep = kBack ? W.bdep : W.fdep;
+        const int k1 = ptr[r + 1];
+        for (int k = ptr[r] + g; k < k1; k += G) {
+            uint16_t ent = dep[k];
+            acc += signed_val<T>(ent, out[ent & kIdx]);
+        }
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o, G);
+    if (r >= 0 && g == 0) {
+        T v;
+        if (kBack) {
             T rv = rvec[r];
             if (alpha != T(0)) {
                 rv -= alpha * W.l[r];
                 rvec[r] = rv;
                 W.xs[r] += alpha * W.h[r];
             }
-            int i0 = W.pivcol[r];
-            int j = W.rowchk[r];
-            T acc = rv;
-            const int e1 = C.h_ptr[j + 1];
-            for (int e = C.h_ptr[j]; e < e1; ++e) {
-                uint16_t ent = W.rowent[e];
-                int i2 = ent & kIdx;
-                if (i2 == i0) continue;
-                uint16_t pr = W.pivrow[i2];
-                if (pr != kNone) acc -= signed_val<T>(ent, out[pr]);
-            }
-            out[r] = W.psgn[r] ? -acc : acc;
+            v = rv - acc;
+        } else {
+            v = out[r] * W.invd2p[r] - acc;
         }
-        __syncthreads();
+        out[r] = W.psgn[r] ? -v : v;
     }
-    const int n = C.n;
-    for (int lev = 1; lev <= L.nf; ++lev) {
-        const int i1 = W.lfptr[lev + 1];
-        for (int idx = W.lfptr[lev] + B.tid; idx < i1; idx += B.nt) {
-            int r = W.lfrows[idx];
-            int i0 = W.pivcol[r];
-            T acc = out[r] * W.invd2p[r];
-            if (i0 < n) {
-                const int k1 = C.v_ptr[i0 + 1];
-                for (int k = C.v_ptr[i0]; k < k1; ++k) {
-                    uint16_t ent = W.colent[k];
-                    if (ent == kNone) continue;
-                    int r2 = ent & kIdx;
-                    if (r2 != r) acc -= signed_val<T>(ent, out[r2]);
+}
+
+// Runs rows level by level. Levels wider than two warps use every thread of
+// the CTA (one row per thread) and a CTA barrier; narrower levels (most of
+// them: the schedules are deep and thin) run on warp 0 with G lanes per row
+// and warp barriers.
+template <typename T, bool kBack>
+__device__ inline void level_sweep(Blk& B, WS<T>& W, const uint32_t* ptr, const uint16_t* rows,
+                                   int nlev, T* rvec, T* out, T alpha) {
+    bool warp_mode = false;
+    for (int lev = 1; lev <= nlev; ++lev) {
+        const int i0 = ptr[lev], i1 = ptr[lev + 1];
+        const int cnt = i1 - i0;
+        if (cnt > 64 && B.nt > 32) {
+            if (warp_mode) __syncthreads();
+            for (int base = i0; base < i1; base += B.nt) {   // uniform trip count per warp
+                int idx = base + B.tid;
+                solve_row<T, kBack>(W, idx < i1 ? rows[idx] : -1, 0, 1, rvec, out, alpha);
+            }
+            __syncthreads();
+            warp_mode = false;
+        } else {
+            if (B.warp == 0) {
+                const int G = cnt <= 4 ? 8 : cnt <= 8 ? 4 : cnt <= 16 ? 2 : 1;
+                const int per = 32 / G;
+                for (int base = i0; base < i1; base += per) {
+                    int idx = base + B.lane / G;
+                    solve_row<T, kBack>(W, idx < i1 ? rows[idx] : -1, B.lane & (G - 1), G, rvec,
+                                        out, alpha);
                 }
+                __syncwarp();
             }
-            out[r] = W.psgn[r] ? -acc : acc;
+            warp_mode = true;
         }
-        __syncthreads();
     }
+    if (warp_mode) __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// a5: M-solve (Section V): A_M f1 = r by back substitution over the upper-
+// triangular order of Algorithm 7, f2 = f1 / d_M^2, then A_M' z = f2 by
+// forward substitution. out[r] first holds the value of r's pivot column in
+// f1, then z_r. If alpha != 0, the PCG update r -= alpha l, xs += alpha h of
+// each row is fused into its back-substitution step.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline void msolve(Blk& B, const CodeView& C, WS<T>& W, const Levels& L,
+                              T* rvec, T* out, T alpha) {
+    level_sweep<T, true>(B, W, W.lbptr, W.lbrows, L.nb, rvec, out, alpha);
+    level_sweep<T, false>(B, W, W.lfptr, W.lfrows, L.nf, rvec, out, alpha);
 }
 
 // l = Q h = A D^2 A' h (matrix-free; t holds D^2 A' h over the standard
@@ -631,6 +763,7 @@ __device__ inline int pcg(Blk& B, const CodeView& C, WS<T>& W, const Frame& F, c
     int it = 0;
     while (sqrt(rr) >= tol * rn0 && it < max_it) {
         double hl = spmv_Q<T>(B, C, W, F, W.h, W.l);
+        if (!(hl > 0.0) || !isfinite(hl)) break;   // lost positive curvature (rounding)
         T alpha = (T)(zr / hl);
         msolve<T>(B, C, W, L, W.r, W.z, alpha);   // fused r -= a l, xs += a h
         double zr_l = 0.0, rr_l = 0.0;
@@ -646,66 +779,270 @@ __device__ inline int pcg(Blk& B, const CodeView& C, WS<T>& W, const Frame& F, c
         __syncthreads();
         ++it;
     }
-    *relres = sqrt(rr) / rn0;
+    *relres = isfinite(rr) ? sqrt(rr) / rn0 : INFINITY;
     return it;
 }
 
 // Newton solve (A D^2 A') dy = w with iterative refinement: each round
-// solves Q d = r64 / ||r64|| by PCG in type T, adds ||r64|| d to the FP64
-// solution dy and recomputes the FP64 residual r64 = w - Q dy with FP64 D^2.
-// Stops at ||r64|| < tol ||w||, when a round no longer halves ||r64||, or
-// when the PCG iteration budget is spent. In FP64 mode one round normally
-// suffices.
-struct NewtonOut { int iters; double relres; };
+// solves Q d = r64 / ||r64|| by PCG, adds ||r64|| d to the FP64 solution dy
+// and recomputes the FP64 residual r64 = w - Q dy with FP64 D^2. Rounds run
+// in type T; in the mixed mode (T = float), once an FP32 round fails to
+// reach its tolerance or to halve ||r64||, the remaining rounds run in FP64
+// (FP32 cannot resolve the preconditioned system once D^2 spreads over many
+// decades near the optimum). Stops at ||r64|| < tol ||w||, when an FP64
+// round no longer halves ||r64||, or when the PCG budget is spent.
+struct NewtonOut { int iters, iters64; double relres; };
+
+template <typename V, typename T>
+__device__ inline void residual64(Blk& B, const CodeView& C, WS<T>& W, const Frame& F, double* rr) {
+    const int n = C.n, p = F.p;
+    for (int i = B.tid; i < n; i += B.nt) W.t64[i] = W.d2[i] * colA_T<double>(C, W, i, W.dy);
+    __syncthreads();
+    double acc = 0.0;
+    for (int r = B.tid; r < p; r += B.nt) {
+        double v = W.w[r] - (rowA<double>(C, W, r, W.t64) + W.d2[n + r] * W.dy[r]);
+        W.r64[r] = v;
+        acc += v * v;
+    }
+    *rr = bsum(B, acc);
+}
+
+template <typename V, typename T>
+__device__ inline int refine_round(Blk& B, const CodeView& C, WS<V>& WV, WS<T>& W, const Frame& F,
+                                   const Levels& L, double rn, double target, int budget,
+                                   double* rel) {
+    const int p = F.p;
+    const double inv = 1.0 / rn;
+    for (int r = B.tid; r < p; r += B.nt) WV.r[r] = (V)(W.r64[r] * inv);
+    __syncthreads();
+    int it = pcg<V>(B, C, WV, F, L, target, budget, rel);
+    int bad = 0;
+    for (int r = B.tid; r < p; r += B.nt) bad |= !isfinite((double)WV.xs[r]);
+    bad = __syncthreads_or(bad);
+    if (bad) {            // overflow in this precision: keep dy, report failure
+        *rel = INFINITY;
+        return it;
+    }
+    for (int r = B.tid; r < p; r += B.nt) W.dy[r] += rn * (double)WV.xs[r];
+    __syncthreads();
+    return it;
+}
 
 template <typename T>
 __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                          const Levels& L, const DevParams& P, double tol,
-                                         int max_it) {
-    const int n = C.n, p = F.p;
+                                         int max_it, bool& force64) {
+    const int p = F.p;
     double ww = 0.0;
     for (int r = B.tid; r < p; r += B.nt) { W.dy[r] = 0.0; W.r64[r] = W.w[r]; ww += W.w[r] * W.w[r]; }
     const double wn = sqrt(bsum(B, ww));
-    NewtonOut o{0, 0.0};
+    NewtonOut o{0, 0, 0.0};
     if (wn == 0.0) return o;
     double rn = wn;
-    for (int round = 0; round < 8; ++round) {
+    bool use64 = sizeof(T) == 8 || force64;
+    bool view_ready = false;
+    const int fp32_cap = max(64, max_it / 8);   // one FP32 round; failing it switches to FP64
+    WS<double> W64;
+    for (int round = 0; round < 12; ++round) {
         if (rn < tol * wn || o.iters >= max_it) break;
-        const double inv = 1.0 / rn;
-        for (int r = B.tid; r < p; r += B.nt) W.r[r] = (T)(W.r64[r] * inv);
-        __syncthreads();
         double target = tol * wn / rn;
-        if (sizeof(T) < 8) target = fmax(target, P.tol_inner);
-        double rel;
-        o.iters += pcg<T>(B, C, W, F, L, target, max_it - o.iters, &rel);
-        for (int r = B.tid; r < p; r += B.nt) W.dy[r] += rn * (double)W.xs[r];
-        __syncthreads();
-        // r64 = w - A D^2 A' dy in FP64
-        for (int i = B.tid; i < n; i += B.nt) W.t64[i] = W.d2[i] * colA_T<double>(C, W, i, W.dy);
-        __syncthreads();
-        double rr = 0.0;
-        for (int r = B.tid; r < p; r += B.nt) {
-            double v = W.w[r] - (rowA<double>(C, W, r, W.t64) + W.d2[n + r] * W.dy[r]);
-            W.r64[r] = v;
-            rr += v * v;
+        double rel = 0.0;
+        int it;
+        if (!use64) {
+            target = fmax(target, P.tol_inner);
+            it = refine_round<T, T>(B, C, W, W, F, L, rn, target, min(fp32_cap, max_it - o.iters),
+                                    &rel);
+        } else if (sizeof(T) == 8) {
+            it = refine_round<T, T>(B, C, W, W, F, L, rn, target, max_it - o.iters, &rel);
+            o.iters64 += it;
+        } else {
+            if (!view_ready) {
+                W64 = fp64_view<T>(W, C.n, C.m);
+                for (int r = B.tid; r < p; r += B.nt) W64.invd2p[r] = 1.0 / W.d2[W.pivcol[r]];
+                __syncthreads();
+                view_ready = true;
+            }
+            it = refine_round<double, T>(B, C, W64, W, F, L, rn, target, max_it - o.iters, &rel);
+            o.iters64 += it;
         }
-        double rn_new = sqrt(bsum(B, rr));
-        bool stalled = !(rn_new < 0.5 * rn);
+        o.iters += it;
+        double rr;
+        residual64<double, T>(B, C, W, F, &rr);
+        double rn_new = sqrt(rr);
+        bool halved = rn_new < 0.5 * rn;
+        bool missed = rel > target;   // PCG stopped at its budget
         rn = rn_new;
-        if (stalled) break;
+        if (!use64) {
+            if (!halved || missed) use64 = force64 = true;   // FP64 from here on in this LP
+        } else if (!halved) {
+            break;
+        }
     }
     o.relres = rn / wn;
     return o;
 }
 
 // ---------------------------------------------------------------------------
-// a3 + a6: infeasible primal-dual path-following method (Section IV-B)
+// Optimality certificate. Section VI-A: the unique LP solution is strictly
+// complementary, its basic set B = {i : x*_i > 0} has linearly independent
+// columns, and near the optimum x_i > z_i exactly on B. Given the partition
+// read from (x, z):
+//   primal  x^_N = 0, A_B x^_B = b (minimum-norm correction of x_B by CGLS);
+//   dual    y^ = y + A_B lam with (A_B' A_B) lam = c_B - A_B' y (CG), so that
+//           z^_B = c_B - A_B' y^ = 0;
+// and x^ >= 0, z^_N = c_N - A_N' y^ >= 0. Primal and dual feasibility with
+// complementarity prove x^ optimal, and since the optimum is unique x^ is it,
+// whatever the accuracy of the iterate it came from. On success x := x^.
 // ---------------------------------------------------------------------------
-struct IpmOut { int iters, pcg_iters, converged, max_levels; };
+template <typename T>
+__device__ __forceinline__ double rowA_basic(const CodeView& C, const WS<T>& W, int r,
+                                             const double* v) {
+    int j = W.rowchk[r];
+    double acc = 0.0;
+    const int e1 = C.h_ptr[j + 1];
+    for (int e = C.h_ptr[j]; e < e1; ++e) {
+        uint16_t ent = W.rowent[e];
+        int i = ent & kIdx;
+        if (W.basic[i]) acc += signed_val<double>(ent, v[i]);
+    }
+    if (W.basic[C.n + r]) acc += v[C.n + r];
+    return acc;
+}
+template <typename T>
+__device__ __forceinline__ double colA_basic(const CodeView& C, const WS<T>& W, int i,
+                                             const double* s) {
+    if (!W.basic[i]) return 0.0;
+    return i < C.n ? colA_T<double>(C, W, i, s) : s[i - C.n];
+}
 
 __device__ __forceinline__ double cost_of(const double* gamma, int n, int i) {
     return i < n ? fabs(gamma[i]) : 0.0;
 }
+
+template <typename T>
+__device__ inline int certify(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                              const double* gamma) {
+    const int n = C.n, p = F.p, q = F.q;
+    double nbasic = 0.0, cmax = 0.0;
+    for (int i = B.tid; i < q; i += B.nt) {
+        uint8_t bi = W.x[i] > W.zz[i] ? 1 : 0;
+        W.basic[i] = bi;
+        nbasic += bi;
+        W.v1[i] = 0.0;
+        W.vx[i] = bi ? W.x[i] : 0.0;
+        cmax = fmax(cmax, cost_of(gamma, n, i));
+    }
+    double2 nb = bsum2(B, nbasic, 0.0);
+    cmax = -bmin2(B, -cmax, 0.0).x;
+    const int max_it = 2 * (int)nb.x + 50;
+    // --- primal: CGLS on A_B d = s, s = b - A_B x_B
+    double* d = W.v1; double* g = W.v2; double* h = W.v3; double* sr = W.vr1; double* lr = W.vr2;
+    double ss = 0.0, bb = 0.0;
+    for (int r = B.tid; r < p; r += B.nt) {
+        double v = W.b[r] - rowA_basic(C, W, r, W.vx);
+        sr[r] = v;
+        ss += v * v;
+        bb += W.b[r] * W.b[r];
+    }
+    double2 t0 = bsum2(B, ss, bb);
+    ss = t0.x;
+    const double pstop = 1e-13 * (1.0 + sqrt(t0.y));
+    double gg = 0.0;
+    for (int i = B.tid; i < q; i += B.nt) {
+        double v = colA_basic(C, W, i, sr);
+        g[i] = v; h[i] = v; gg += v * v;
+    }
+    gg = bsum(B, gg);
+    for (int it = 0; it < max_it && sqrt(ss) > pstop && gg > 0.0; ++it) {
+        double ll = 0.0;
+        for (int r = B.tid; r < p; r += B.nt) {
+            double v = rowA_basic(C, W, r, h);
+            lr[r] = v; ll += v * v;
+        }
+        ll = bsum(B, ll);
+        if (!(ll > 0.0)) break;
+        const double a = gg / ll;
+        for (int i = B.tid; i < q; i += B.nt) d[i] += a * h[i];
+        double sl = 0.0;
+        for (int r = B.tid; r < p; r += B.nt) { double v = sr[r] - a * lr[r]; sr[r] = v; sl += v * v; }
+        ss = bsum(B, sl);
+        double gl = 0.0;
+        for (int i = B.tid; i < q; i += B.nt) { double v = colA_basic(C, W, i, sr); g[i] = v; gl += v * v; }
+        const double gg2 = bsum(B, gl);
+        const double beta = gg2 / gg;
+        gg = gg2;
+        for (int i = B.tid; i < q; i += B.nt) h[i] = g[i] + beta * h[i];
+        __syncthreads();
+    }
+    double mnx = INFINITY;
+    for (int i = B.tid; i < q; i += B.nt) {
+        double v = W.basic[i] ? W.vx[i] + d[i] : 0.0;
+        W.vx[i] = v;
+        if (W.basic[i]) mnx = fmin(mnx, v);
+    }
+    __syncthreads();
+    double res = 0.0;
+    for (int r = B.tid; r < p; r += B.nt)
+        res = fmax(res, fabs(rowA<double>(C, W, r, W.vx) + W.vx[n + r] - W.b[r]));
+    double2 pm = bmin2(B, mnx, -res);
+    if (!(pm.x >= -1e-11 && -pm.y <= 1e-9)) return 0;
+    // --- dual: CG on (A_B' A_B) lam = t, t = c_B - A_B' y
+    double* lam = W.v1; double* rq = W.v2; double* pq = W.v3; double* kq = W.v4;
+    double* ap = W.vr1; double* yh = W.vr2;
+    double rr = 0.0, tt = 0.0;
+    for (int i = B.tid; i < q; i += B.nt) {
+        double v = 0.0;
+        if (W.basic[i]) {
+            double aty = (i < n) ? colA_T<double>(C, W, i, W.y) : W.y[i - n];
+            v = cost_of(gamma, n, i) - aty;
+        }
+        lam[i] = 0.0; rq[i] = v; pq[i] = v; rr += v * v;
+        tt += cost_of(gamma, n, i) * cost_of(gamma, n, i);
+    }
+    double2 t1 = bsum2(B, rr, tt);
+    rr = t1.x;
+    const double dstop = 1e-13 * (1.0 + sqrt(t1.y));
+    for (int it = 0; it < max_it && sqrt(rr) > dstop; ++it) {
+        for (int r = B.tid; r < p; r += B.nt) ap[r] = rowA_basic(C, W, r, pq);
+        __syncthreads();
+        double pkp = 0.0;
+        for (int i = B.tid; i < q; i += B.nt) { double v = colA_basic(C, W, i, ap); kq[i] = v; pkp += pq[i] * v; }
+        pkp = bsum(B, pkp);
+        if (!(pkp > 0.0)) break;
+        const double a = rr / pkp;
+        double rl = 0.0;
+        for (int i = B.tid; i < q; i += B.nt) {
+            lam[i] += a * pq[i];
+            double v = rq[i] - a * kq[i];
+            rq[i] = v; rl += v * v;
+        }
+        const double rr2 = bsum(B, rl);
+        const double beta = rr2 / rr;
+        rr = rr2;
+        for (int i = B.tid; i < q; i += B.nt) pq[i] = rq[i] + beta * pq[i];
+        __syncthreads();
+    }
+    for (int r = B.tid; r < p; r += B.nt) yh[r] = W.y[r] + rowA_basic(C, W, r, lam);
+    __syncthreads();
+    double zmin_n = INFINITY, zmax_b = 0.0;
+    for (int i = B.tid; i < q; i += B.nt) {
+        double aty = (i < n) ? colA_T<double>(C, W, i, yh) : yh[i - n];
+        double zi = cost_of(gamma, n, i) - aty;
+        if (W.basic[i]) zmax_b = fmax(zmax_b, fabs(zi));
+        else zmin_n = fmin(zmin_n, zi);
+    }
+    double2 dm = bmin2(B, zmin_n, -zmax_b);
+    const double scale = 1.0 + cmax;
+    if (!(dm.x >= -1e-11 * scale && -dm.y <= 1e-8 * scale)) return 0;
+    for (int i = B.tid; i < q; i += B.nt) W.x[i] = W.vx[i];
+    __syncthreads();
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// a3 + a6: infeasible primal-dual path-following method (Section IV-B)
+// ---------------------------------------------------------------------------
+struct IpmOut { int iters, pcg_iters, pcg_iters64, converged, certified, max_levels; };
 
 // trace (optional): per iteration 8 doubles {gap, feas_p, feas_d, PCG
 // iterations, Newton relative residual, beta_P, beta_D, levels}
@@ -714,7 +1051,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
                                    const DevParams& P, const double* gamma, int q2,
                                    double* trace = nullptr, int max_trace = 0) {
     const int n = C.n, p = F.p, q = F.q;
-    IpmOut o{0, 0, 0, 0};
+    IpmOut o{0, 0, 0, 0, 0, 0};
     // cold start x = e, y = 0, z = c + e
     double nc2 = 0.0;
     for (int i = B.tid; i < q; i += B.nt) {
@@ -725,7 +1062,25 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
     }
     for (int r = B.tid; r < p; r += B.nt) W.y[r] = 0.0;
     F.normc = sqrt(bsum(B, nc2));   // (barrier inside)
+    double prev_grel = INFINITY, sig0 = -1.0, sig1 = -1.0;
+    bool force64 = false;
     for (int it = 0;; ++it) {
+        // once the gap is small and the partition x_i > z_i stopped moving,
+        // try to certify the optimal vertex
+        if (prev_grel < P.tol_cert) {
+            double c0 = 0.0, c1 = 0.0;
+            for (int i = B.tid; i < q; i += B.nt)
+                if (W.x[i] > W.zz[i]) { c0 += 1.0; c1 += (double)(i + 1) * (double)(i + 1); }
+            double2 sg = bsum2(B, c0, c1);
+            if (sg.x == sig0 && sg.y == sig1 && certify<T>(B, C, W, F, gamma)) {
+                o.converged = 1;
+                o.certified = 1;
+                o.iters = it;
+                break;
+            }
+            sig0 = sg.x;
+            sig1 = sg.y;
+        }
         // residuals r_b = b - A x (into W.w), r_c = c - A'y - z (into W.rc)
         double nrb2 = 0.0;
         for (int r = B.tid; r < p; r += B.nt) {
@@ -779,8 +1134,13 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
         }
         __syncthreads();
         const double tol = fmax(P.tol_pcg, fmin(1e-3, P.pcg_gap_factor * g_rel));
-        NewtonOut no = newton_solve<T>(B, C, W, F, L, P, tol, P.max_pcg);
+        NewtonOut no = newton_solve<T>(B, C, W, F, L, P, tol, P.max_pcg, force64);
         o.pcg_iters += no.iters;
+        o.pcg_iters64 += no.iters64;
+        if (no.relres > 1e-3 && g_rel < P.tol_cert) {   // no usable direction left
+            o.iters = it;
+            break;
+        }
         // Newton direction (Eqs. 25-26), with r_c recomputed from (x, y, z)
         double ap = INFINITY, ad = INFINITY;
         for (int i = B.tid; i < q; i += B.nt) {
@@ -811,6 +1171,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
         }
         for (int r = B.tid; r < p; r += B.nt) W.y[r] += bd * W.dy[r];
         __syncthreads();
+        prev_grel = g_rel;
     }
     return o;
 }
@@ -973,11 +1334,13 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
         st.alp_iters++;
         st.ipm_iters_total += io.iters;
         st.pcg_iters_total += io.pcg_iters;
+        st.pcg_iters_fp64 += io.pcg_iters64;
         st.max_levels = max(st.max_levels, io.max_levels);
-        st.vertex_failures += vertex_recover<T>(B, C, W, F, gamma);
+        int ok = io.certified || certify<T>(B, C, W, F, gamma);
+        if (!ok) st.vertex_failures += vertex_recover<T>(B, C, W, F, gamma);
         lp_finish<T>(B, C, W, F, P);
         st.lp_rows_final = F.p;
-        if (!io.converged) { status = LPDEC_ERR_NOT_CONVERGED; break; }
+        if (!io.converged && !ok) { status = LPDEC_ERR_NOT_CONVERGED; break; }
     }
     // a7: outputs. cert = integral; hard_i = [u_i > 1/2], the channel's
     // decision where u_i is within tau_int of 1/2.

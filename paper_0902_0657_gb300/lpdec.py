@@ -33,7 +33,7 @@ LPDEC_MIXED = 1
 class lpdec_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("sigma", "eta", "tol_gap", "tol_feas", "tol_pcg", "tau_act", "tau_cut", "tau_int",
-                 "pcg_gap_factor", "tol_inner", "tol_feas_loose")] + \
+                 "pcg_gap_factor", "tol_inner", "tol_feas_loose", "tol_cert")] + \
                [(k, ctypes.c_int32) for k in
                 ("max_alp", "max_ipm", "max_pcg", "variant", "precision",
                  "threads_per_block", "smem_budget", "reserved")]
@@ -42,12 +42,12 @@ class lpdec_params(ctypes.Structure):
 class lpdec_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in
                 ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total", "lp_rows_final",
-                 "vertex_failures", "max_levels", "reserved")] + [("objective", ctypes.c_double)]
+                 "vertex_failures", "max_levels", "pcg_iters_fp64")] + [("objective", ctypes.c_double)]
 
 
 STATS_DTYPE = np.dtype([(k, np.int32) for k in
                         ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total",
-                         "lp_rows_final", "vertex_failures", "max_levels", "reserved")] +
+                         "lp_rows_final", "vertex_failures", "max_levels", "pcg_iters_fp64")] +
                        [("objective", np.float64)])
 assert STATS_DTYPE.itemsize == ctypes.sizeof(lpdec_stats)
 
