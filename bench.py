@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 adaptive LP decoder.
+
+Metric: LP-decoded frames/s on the (3,6)-regular n=1008, m=504 LDPC code
+(PEG-style construction, seed 0) over BPSK/AWGN at Eb/N0 = 2.0 dB, all-zero
+codeword, gamma = 2y/sigma^2. The job draws its frames from a pool of 20,000
+synthetic frames (seed 0); one step decodes --frames distinct frames per GPU
+through one persistent kernel launch (MALP-A + interior point + PCG + MTS for
+every frame). Inputs are resident in HBM when the timed region starts; L2 is
+flushed (256 MB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank decodes its own frames (weak scaling, no
+collective on the data path); rank 0 prints one JSON line. --impl reference
+times the CPU oracle (FP64, dense Cholesky interior point) on the host cores
+on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LP-decoded frames/s at n=1008 (3,6) LDPC 2 dB; p99 latency; PCG SpMV HBM GB/s"
+UNIT = "frames/s"
+CODE_NAME = "peg_1008"
+EBN0_DB = 2.0
+POOL = 20000
+SEED = 0
+# FP64 peak of the GB300 FP64 units: 1.25 TFLOP/s nominal at the 2070 MHz
+# maximum SM clock over 152 SMs, i.e. 4 FP64 flops per SM per clock.
+FP64_FLOPS_PER_SM_CLK = 4.0
+N_SMS = 152
+# DRAM bytes per k_decode launch from an ncu capture of this workload
+# (profiles/k_decode_peg1008.md); None until captured for the current kernel.
+DECODE_TRAFFIC_BYTES = None
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=4096, help="frames per step per GPU")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--threads", type=int, default=128)
+    ap.add_argument("--oracle-seconds", type=float, default=15.0,
+                    help="CPU seconds per oracle worker for the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, n, m):
+    return {
+        "workload": f"(3,6) PEG LDPC n={n} m={m}, BPSK/AWGN Eb/N0 {EBN0_DB} dB, all-zero codeword, "
+                    f"{POOL}-frame pool (seed {SEED}), {args.frames} frames per step per GPU",
+        "code": CODE_NAME, "n": n, "m": m, "ebn0_db": EBN0_DB, "pool_frames": POOL,
+        "frames_per_step": args.frames, "precision": args.precision,
+        "threads_per_block": args.threads, "variant": "MALP-A",
+        "l2": "flushed by a 256 MB write between timed steps",
+    }
+
+
+def frame_ids(step, rank, world, per_step):
+    base = (step * world + rank) * per_step
+    return [(base + i) % POOL for i in range(per_step)]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (spawned worker processes, one BLAS thread each)
+# ---------------------------------------------------------------------------
+
+def _oracle_worker(args):
+    wid, nworkers, seconds, frames = args
+    import numpy as np  # noqa: F401
+    import oracle
+    from synth import awgn_llr_frames, named_code
+    code = named_code(CODE_NAME)
+    t0 = time.perf_counter()
+    done = 0
+    for f in frames[wid::nworkers]:
+        g = awgn_llr_frames(code.n, code.design_rate, EBN0_DB, SEED, [f])[0]
+        oracle.decode(code, g)
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return done, time.perf_counter() - t0
+
+
+def run_oracle_sample(seconds, offset):
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    cores = os.cpu_count() or 1
+    frames = [(offset + i) % POOL for i in range(10 * cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(w, cores, seconds, frames) for w in range(cores)])
+    done = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return done, wall, cores
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+        return False
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+
+    from paper_0902_0657_gb300 import build as B
+    from paper_0902_0657_gb300 import lpdec as L
+    from synth import awgn_llr_frames, named_code
+
+    B.build()
+    code = named_code(CODE_NAME)
+    n, m, B_ = code.n, code.m, args.frames
+    prm = L.lpdec_default_params()
+    prm.precision = L.LPDEC_MIXED if args.precision == "mixed" else L.LPDEC_FP64
+    prm.threads_per_block = args.threads
+    dec = L.Decoder(code, device=local, params=prm)
+
+    nsteps = args.warmup + args.steps
+    gam = [torch.from_numpy(awgn_llr_frames(n, code.design_rate, EBN0_DB, SEED,
+                                            frame_ids(k, rank, world, B_))).cuda()
+           for k in range(nsteps)]
+    d_u = torch.empty((B_, n), dtype=torch.float64, device="cuda")
+    d_h = torch.empty((B_, n), dtype=torch.uint8, device="cuda")
+    d_c = torch.empty(B_, dtype=torch.int32, device="cuda")
+    d_m = torch.empty((B_, m), dtype=torch.int32, device="cuda")
+    d_s = torch.empty(B_ * L.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        rc = L.lpdec_decode_batch_device(dec.ctx, dec.code, B_, gam[k], d_u, d_h, d_c, d_m, d_s,
+                                         stream=stream)
+        if rc != 0:
+            raise RuntimeError(f"decode failed: {L.error_string(rc)}")
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    times, flops, stats_all = [], 0.0, []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.warmup, nsteps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(k)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            st = d_s.cpu().numpy().view(L.STATS_DTYPE)
+            stats_all.append(st.copy())
+            flops += float(st["pcg_flops"].sum())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    t_total = sum(times)
+    t_max = t_total
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    frames_total = B_ * args.steps * world
+    value = frames_total / t_max
+
+    # end to end through the host API (pinned host buffers, copies inside)
+    e2e = None
+    if not args.no_e2e:
+        g_host = torch.empty((B_, n), dtype=torch.float64, pin_memory=True)
+        g_host.copy_(gam[nsteps - 1].cpu())
+        gh = g_host.numpy()
+        u = torch.empty((B_, n), dtype=torch.float64, pin_memory=True).numpy()
+        hd = torch.empty((B_, n), dtype=torch.uint8, pin_memory=True).numpy()
+        ce = torch.empty(B_, dtype=torch.int32, pin_memory=True).numpy()
+        mk = torch.empty((B_, m), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        ss = np.empty(B_, L.STATS_DTYPE)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        rc = L.lpdec_decode_batch(dec.ctx, dec.code, B_, gh, u, hd, ce, mk, ss)
+        te = time.perf_counter() - t0
+        if rc != 0:
+            raise RuntimeError(f"host decode failed: {L.error_string(rc)}")
+        if world > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": B_ * world / te, "unit": UNIT, "h2d_bytes_per_step": B_ * n * 8,
+               "d2h_bytes_per_step": B_ * (n * 8 + n + 4 + m * 4 + L.STATS_DTYPE.itemsize)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        dec.close()
+        return
+
+    st = np.concatenate(stats_all)
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
+    peak = N_SMS * FP64_FLOPS_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    achieved = flops / t_total / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": DECODE_TRAFFIC_BYTES,
+                "kernel": "k_decode (persistent, one CTA per frame)",
+                "peak_source": "FP64 units: 4 flop/SM/clk x 152 SMs x median SM clock (derived)"}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        done, w, cores = run_oracle_sample(args.oracle_seconds, offset=0)
+        cpu = {"value": done / w, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{done} frames of the same workload (pool frames from 0), "
+                         f"{cores} spawned single-threaded workers, ~{args.oracle_seconds:.0f} s each"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic", "config": workload_config(args, n, m),
+        "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
+        "roofline": roofline, "cpu_baseline": cpu,
+        "detail": {
+            "frames_integral": float((st["status"] == 0).mean()) if st.size else None,
+            "frames_not_converged": int((st["status"] != 0).sum()),
+            "mean_lps_per_frame": float(st["alp_iters"].mean()),
+            "mean_ipm_iters_per_frame": float(st["ipm_iters_total"].mean()),
+            "mean_pcg_iters_per_frame": float(st["pcg_iters_total"].mean()),
+            "pcg_flops_per_step": flops / args.steps,
+            "wall_s": wall,
+        },
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    dec.close()
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the CPU oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth import named_code
+    code = named_code(CODE_NAME)
+    total_done, total_wall, cores = 0, 0.0, 1
+    for k in range(args.warmup + args.steps):
+        done, w, cores = run_oracle_sample(args.oracle_seconds, offset=k * 997)
+        if k >= args.warmup:
+            total_done += done
+            total_wall += w
+    value = total_done / total_wall
+    sample = (f"{total_done} frames over {args.steps} timed steps, {cores} spawned "
+              f"single-threaded oracle workers, ~{args.oracle_seconds:.0f} s per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args, code.n, code.m),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

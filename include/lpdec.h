@@ -77,10 +77,10 @@ extern "C" {
  *   tol_feas_loose = 1e-6  the IPM also stops when the gap is below tol_gap and
  *                     both infeasibilities are below this (limited accuracy of
  *                     the Newton solves near the optimum)
- *   tol_cert = 1e-6   below this gap, whenever the partition x_i > z_i is the
- *                     same as one iteration earlier, the decoder tries to
- *                     certify the optimal vertex (primal and dual feasible,
- *                     complementary) and stops the IPM if it succeeds
+ *   tol_cert = 1e-3   below this gap, each interior-point iteration tries to
+ *                     certify the basis of its MTS selection as optimal
+ *                     (x_M = A_M^-1 b >= 0, reduced costs >= 0, complementary;
+ *                     two triangular solves) and stops if it succeeds
  *   tau_act  = 1e-9   an inequality is active iff its slack <= tau_act
  *   tau_cut  = 1e-9   a check is violated iff Eq. 6's left side < 1 - tau_cut
  *   tau_int  = 1e-9   u is integral iff max |u_i - round(u_i)| <= tau_int
@@ -115,6 +115,9 @@ typedef struct lpdec_stats {
     int32_t max_levels;       /* deepest triangular-solve level schedule seen */
     int32_t pcg_iters_fp64;   /* PCG iterations run in FP64 (all of them in LPDEC_FP64) */
     double  objective;        /* gamma'u */
+    double  pcg_flops;        /* algorithmic floating-point operations of the PCG
+                                 iterations (Q h, both triangular solves, dots,
+                                 updates) and the FP64 residuals of refinement */
 } lpdec_stats;
 
 typedef struct lpdec_ctx lpdec_ctx;    /* opaque: device, streams, scratch */

@@ -119,7 +119,7 @@ k_mts_select(CodeView C0, DevParams P, Layout L, const double* gamma, const uint
         if (f >= nframes) break;
         load_lp_state<T>(B, C, W, gamma + (size_t)f * C.n, in_lp + (size_t)f * C.m,
                          mask + (size_t)f * C.m);
-        Frame F{0, C.n, 0.0, 0.0};
+        Frame F{0, C.n, 0.0, 0.0, 0};
         lp_build<T>(B, C, W, F, ks.shscan);
         for (int i = B.tid; i < F.q; i += B.nt) W.d2[i] = wts[(size_t)f * qm + i];
         __syncthreads();
@@ -141,7 +141,7 @@ k_pcg(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in
         if (f >= nframes) break;
         load_lp_state<T>(B, C, W, gamma + (size_t)f * C.n, in_lp + (size_t)f * C.m,
                          mask + (size_t)f * C.m);
-        Frame F{0, C.n, 0.0, 0.0};
+        Frame F{0, C.n, 0.0, 0.0, 0};
         lp_build<T>(B, C, W, F, ks.shscan);
         for (int i = B.tid; i < F.q; i += B.nt) W.d2[i] = d2[(size_t)f * qm + i];
         for (int r = B.tid; r < F.p; r += B.nt) W.w[r] = wv[(size_t)f * C.m + r];
@@ -170,7 +170,7 @@ k_lp_solve(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_
         if (f >= nframes) break;
         const double* g = gamma + (size_t)f * C.n;
         load_lp_state<T>(B, C, W, g, in_lp + (size_t)f * C.m, mask + (size_t)f * C.m);
-        Frame F{0, C.n, 0.0, 0.0};
+        Frame F{0, C.n, 0.0, 0.0, 0};
         lp_build<T>(B, C, W, F, ks.shscan);
         lpdec_stats st{};
         if (F.p > 0) {
@@ -182,6 +182,7 @@ k_lp_solve(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_
             st.ipm_iters_total = io.iters;
             st.pcg_iters_total = io.pcg_iters;
             st.pcg_iters_fp64 = io.pcg_iters64;
+            st.pcg_flops = io.flops;
             st.max_levels = io.max_levels;
             st.status = (io.converged || ok) ? LPDEC_OK : LPDEC_ERR_NOT_CONVERGED;
         } else {
@@ -438,7 +439,7 @@ void lpdec_default_params(lpdec_params* p) {
     p->pcg_gap_factor = 0.01;
     p->tol_inner = 1e-5;
     p->tol_feas_loose = 1e-6;
-    p->tol_cert = 1e-6;
+    p->tol_cert = 1e-3;
     p->max_alp = 200;
     p->max_ipm = 200;
     p->max_pcg = 2000;

@@ -259,6 +259,7 @@ struct Frame {
     int p;          // LP rows
     int q;          // n + p
     double normb, normc;
+    int ea;         // nonzeros of the standard part of A (sum of the LP rows' degrees)
 };
 
 // u^0 = bitwise hard decision (Eq. 8); empty cut set.
@@ -353,9 +354,10 @@ __device__ inline void lp_build(Blk& B, const CodeView& C, WS<T>& W, Frame& F, i
         uint16_t r = W.chkrow[C.v_chk[k]];
         W.colent[k] = (r == kNone) ? kNone : (uint16_t)(r | (W.rowent[C.v_eidx[k]] & kNeg));
     }
-    double nb2 = 0.0;
+    double nb2 = 0.0, ea = 0.0;
     for (int r = B.tid; r < F.p; r += B.nt) {
         int j = W.rowchk[r];
+        ea += C.h_ptr[j + 1] - C.h_ptr[j];
         uint32_t V = W.mask[j];
         double shift = 0.0;
         for (int e = C.h_ptr[j]; e < C.h_ptr[j + 1]; ++e)
@@ -364,7 +366,9 @@ __device__ inline void lp_build(Blk& B, const CodeView& C, WS<T>& W, Frame& F, i
         W.b[r] = bv;
         nb2 += bv * bv;
     }
-    F.normb = sqrt(bsum(B, nb2));   // (barrier inside)
+    double2 t = bsum2(B, nb2, ea);   // (barrier inside)
+    F.normb = sqrt(t.x);
+    F.ea = (int)t.y;
 }
 
 // (A' v)_i for a standard column i (its LP rows, through colent).
@@ -641,7 +645,7 @@ __device__ inline void selection_order(Blk& B, WS<T>& W, const Frame& F, int32_t
 // of the row's dependencies and the leader (g == 0) finishes the row. Back:
 // out[r] = +-(r_r - sum); forward: out[r] = +-(out[r] / d_piv - sum). All 32
 // lanes of the warp call this (r < 0 marks an idle group).
-template <typename T, bool kBack>
+template <typename T, bool kBack, bool kScale = true>
 __device__ __forceinline__ void solve_row(WS<T>& W, int r, int g, int G, T* rvec, T* out,
                                           T alpha) {
     T acc = T(0);
@@ -666,7 +670,7 @@ __device__ __forceinline__ void solve_row(WS<T>& W, int r, int g, int G, T* rvec
             }
             v = rv - acc;
         } else {
-            v = out[r] * W.invd2p[r] - acc;
+            v = (kScale ? out[r] * W.invd2p[r] : out[r]) - acc;
         }
         out[r] = W.psgn[r] ? -v : v;
     }
@@ -676,7 +680,7 @@ __device__ __forceinline__ void solve_row(WS<T>& W, int r, int g, int G, T* rvec
 // the CTA (one row per thread) and a CTA barrier; narrower levels (most of
 // them: the schedules are deep and thin) run on warp 0 with G lanes per row
 // and warp barriers.
-template <typename T, bool kBack>
+template <typename T, bool kBack, bool kScale = true>
 __device__ inline void level_sweep(Blk& B, WS<T>& W, const uint32_t* ptr, const uint16_t* rows,
                                    int nlev, T* rvec, T* out, T alpha) {
     bool warp_mode = false;
@@ -687,7 +691,7 @@ __device__ inline void level_sweep(Blk& B, WS<T>& W, const uint32_t* ptr, const 
             if (warp_mode) __syncthreads();
             for (int base = i0; base < i1; base += B.nt) {   // uniform trip count per warp
                 int idx = base + B.tid;
-                solve_row<T, kBack>(W, idx < i1 ? rows[idx] : -1, 0, 1, rvec, out, alpha);
+                solve_row<T, kBack, kScale>(W, idx < i1 ? rows[idx] : -1, 0, 1, rvec, out, alpha);
             }
             __syncthreads();
             warp_mode = false;
@@ -697,8 +701,8 @@ __device__ inline void level_sweep(Blk& B, WS<T>& W, const uint32_t* ptr, const 
                 const int per = 32 / G;
                 for (int base = i0; base < i1; base += per) {
                     int idx = base + B.lane / G;
-                    solve_row<T, kBack>(W, idx < i1 ? rows[idx] : -1, B.lane & (G - 1), G, rvec,
-                                        out, alpha);
+                    solve_row<T, kBack, kScale>(W, idx < i1 ? rows[idx] : -1, B.lane & (G - 1), G,
+                                                rvec, out, alpha);
                 }
                 __syncwarp();
             }
@@ -791,7 +795,15 @@ __device__ inline int pcg(Blk& B, const CodeView& C, WS<T>& W, const Frame& F, c
 // (FP32 cannot resolve the preconditioned system once D^2 spreads over many
 // decades near the optimum). Stops at ||r64|| < tol ||w||, when an FP64
 // round no longer halves ||r64||, or when the PCG budget is spent.
-struct NewtonOut { int iters, iters64; double relres; };
+struct NewtonOut { int iters, iters64; double relres, flops; };
+
+// Algorithmic floating-point operations of one PCG iteration (Algorithm 4):
+// Q h (2 passes over the pattern, D^2 and the slacks), the two triangular
+// solves (one multiply-add per dependency, pivot scaling), three dot
+// products and the vector updates.
+__device__ __forceinline__ double pcg_iter_flops(const Frame& F, int n, int deps) {
+    return 4.0 * F.ea + 2.0 * deps + n + 15.0 * F.p;
+}
 
 template <typename V, typename T>
 __device__ inline void residual64(Blk& B, const CodeView& C, WS<T>& W, const Frame& F, double* rr) {
@@ -836,8 +848,9 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
     double ww = 0.0;
     for (int r = B.tid; r < p; r += B.nt) { W.dy[r] = 0.0; W.r64[r] = W.w[r]; ww += W.w[r] * W.w[r]; }
     const double wn = sqrt(bsum(B, ww));
-    NewtonOut o{0, 0, 0.0};
+    NewtonOut o{0, 0, 0.0, 0.0};
     if (wn == 0.0) return o;
+    const double it_flops = pcg_iter_flops(F, C.n, (int)(W.bptr[p] + W.fptr[p]));
     double rn = wn;
     bool use64 = sizeof(T) == 8 || force64;
     bool view_ready = false;
@@ -866,6 +879,7 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
             o.iters64 += it;
         }
         o.iters += it;
+        o.flops += it * it_flops + 4.0 * F.ea + C.n + 3.0 * p;
         double rr;
         residual64<double, T>(B, C, W, F, &rr);
         double rn_new = sqrt(rr);
@@ -934,7 +948,7 @@ __device__ inline int certify(Blk& B, const CodeView& C, WS<T>& W, const Frame& 
     }
     double2 nb = bsum2(B, nbasic, 0.0);
     cmax = -bmin2(B, -cmax, 0.0).x;
-    const int max_it = 2 * (int)nb.x + 50;
+    const int max_it = min(2 * (int)nb.x + 50, 1000);
     // --- primal: CGLS on A_B d = s, s = b - A_B x_B
     double* d = W.v1; double* g = W.v2; double* h = W.v3; double* sr = W.vr1; double* lr = W.vr2;
     double ss = 0.0, bb = 0.0;
@@ -1039,10 +1053,68 @@ __device__ inline int certify(Blk& B, const CodeView& C, WS<T>& W, const Frame& 
     return 1;
 }
 
+// Certificate from the MTS basis. The p selected columns M form a
+// nonsingular (triangular) basis of A. Near the optimum of an integral LP
+// they contain the basic set B, and then
+//   x_M = A_M^-1 b  (one back substitution)
+// is the optimal vertex. The dual is pinned to the iterate's partition:
+// z^_i = 0 for basic i in M, z^_i = c_i - (A'y)_i for the other columns of
+// M, and A_M' y^ = c_M - z^_M (one forward substitution). If x^ >= 0,
+// z^ = c - A'y^ >= 0 on every column and x^_i z^_i = 0, the pair is primal
+// and dual feasible and complementary, so x^ is optimal (and, the optimum
+// being unique, the vertex the oracle reaches). On success x := x^.
+template <typename T>
+__device__ inline int certify_basis(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                                    const Levels& L, const double* gamma) {
+    const int n = C.n, p = F.p, q = F.q;
+    WS<double> D = fp64_view<T>(W, n, C.m);
+    double* rhs = W.vr1;
+    double* out = W.vr2;
+    double cmax = 0.0;
+    for (int r = B.tid; r < p; r += B.nt) rhs[r] = W.b[r];
+    for (int i = B.tid; i < q; i += B.nt) cmax = fmax(cmax, cost_of(gamma, n, i));
+    __syncthreads();
+    level_sweep<double, true>(B, D, W.lbptr, W.lbrows, L.nb, rhs, out, 0.0);
+    // x^ over the columns (pivot column of row r gets out[r])
+    double mnx = INFINITY;
+    for (int i = B.tid; i < q; i += B.nt) W.vx[i] = 0.0;
+    __syncthreads();
+    for (int r = B.tid; r < p; r += B.nt) {
+        double v = out[r];
+        W.vx[W.pivcol[r]] = v;
+        mnx = fmin(mnx, v);
+    }
+    // right side of A_M' y^ = c_M - z^_M, indexed by the pivot row
+    for (int r = B.tid; r < p; r += B.nt) {
+        int i = W.pivcol[r];
+        double c = cost_of(gamma, n, i);
+        double zt = 0.0;
+        if (!(W.x[i] > W.zz[i])) zt = c - ((i < n) ? colA_T<double>(C, W, i, W.y) : W.y[i - n]);
+        out[r] = c - zt;
+    }
+    double2 m0 = bmin2(B, mnx, -cmax);
+    cmax = -m0.y;
+    const double tol = 1e-11 * (1.0 + cmax);
+    if (!(m0.x >= -tol)) return 0;
+    level_sweep<double, false, false>(B, D, W.lfptr, W.lfrows, L.nf, rhs, out, 0.0);
+    double zmin = INFINITY, comp = 0.0;
+    for (int i = B.tid; i < q; i += B.nt) {
+        double aty = (i < n) ? colA_T<double>(C, W, i, out) : out[i - n];
+        double zi = cost_of(gamma, n, i) - aty;
+        zmin = fmin(zmin, zi);
+        comp = fmax(comp, fabs(W.vx[i] * zi));
+    }
+    double2 m1 = bmin2(B, zmin, -comp);
+    if (!(m1.x >= -tol && -m1.y <= tol)) return 0;
+    for (int i = B.tid; i < q; i += B.nt) W.x[i] = fmax(W.vx[i], 0.0);
+    __syncthreads();
+    return 1;
+}
+
 // ---------------------------------------------------------------------------
 // a3 + a6: infeasible primal-dual path-following method (Section IV-B)
 // ---------------------------------------------------------------------------
-struct IpmOut { int iters, pcg_iters, pcg_iters64, converged, certified, max_levels; };
+struct IpmOut { int iters, pcg_iters, pcg_iters64, converged, certified, max_levels; double flops; };
 
 // trace (optional): per iteration 8 doubles {gap, feas_p, feas_d, PCG
 // iterations, Newton relative residual, beta_P, beta_D, levels}
@@ -1051,7 +1123,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
                                    const DevParams& P, const double* gamma, int q2,
                                    double* trace = nullptr, int max_trace = 0) {
     const int n = C.n, p = F.p, q = F.q;
-    IpmOut o{0, 0, 0, 0, 0, 0};
+    IpmOut o{0, 0, 0, 0, 0, 0, 0.0};
     // cold start x = e, y = 0, z = c + e
     double nc2 = 0.0;
     for (int i = B.tid; i < q; i += B.nt) {
@@ -1062,12 +1134,17 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
     }
     for (int r = B.tid; r < p; r += B.nt) W.y[r] = 0.0;
     F.normc = sqrt(bsum(B, nc2));   // (barrier inside)
-    double prev_grel = INFINITY, sig0 = -1.0, sig1 = -1.0;
     bool force64 = false;
+    int last_pcg = 0;
+    double prev_grel = INFINITY, sig0 = -1.0, sig1 = -1.0;
     for (int it = 0;; ++it) {
-        // once the gap is small and the partition x_i > z_i stopped moving,
-        // try to certify the optimal vertex
-        if (prev_grel < P.tol_cert) {
+        // Expensive regime (the basis certificate keeps failing and Newton
+        // solves need hundreds of PCG iterations, typical of LPs with a
+        // fractional optimum): once the gap is small and the partition
+        // x_i > z_i has not moved for an iteration, try the general
+        // certificate (CG on the basic columns), far cheaper than one more
+        // interior-point iteration here.
+        if (prev_grel < 1e-5 && last_pcg > 200) {
             double c0 = 0.0, c1 = 0.0;
             for (int i = B.tid; i < q; i += B.nt)
                 if (W.x[i] > W.zz[i]) { c0 += 1.0; c1 += (double)(i + 1) * (double)(i + 1); }
@@ -1127,6 +1204,13 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
         __syncthreads();
         Levels L = mts_select<T>(B, C, W, F, W.d2, q2);
         o.max_levels = max(o.max_levels, max(L.nb, L.nf));
+        // near the optimum the selected basis may already be optimal
+        if (g_rel < P.tol_cert && certify_basis<T>(B, C, W, F, L, gamma)) {
+            o.converged = 1;
+            o.certified = 1;
+            o.iters = it;
+            break;
+        }
         for (int i = B.tid; i < q; i += B.nt) W.d2t[i] = (T)W.d2[i];
         for (int r = B.tid; r < p; r += B.nt) {
             int pc = W.pivcol[r];
@@ -1137,7 +1221,9 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
         NewtonOut no = newton_solve<T>(B, C, W, F, L, P, tol, P.max_pcg, force64);
         o.pcg_iters += no.iters;
         o.pcg_iters64 += no.iters64;
-        if (no.relres > 1e-3 && g_rel < P.tol_cert) {   // no usable direction left
+        o.flops += no.flops;
+        last_pcg = no.iters;
+        if (no.relres > 1e-3 && g_rel < 1e-6) {   // no usable direction left near the optimum
             o.iters = it;
             break;
         }
@@ -1312,7 +1398,7 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
     int bad = 0;
     for (int i = B.tid; i < C.n; i += B.nt) bad |= !isfinite(gamma[i]);
     bad = __syncthreads_or(bad);
-    Frame F{0, C.n, 0.0, 0.0};
+    Frame F{0, C.n, 0.0, 0.0, 0};
     lpdec_stats st{};
     if (bad) {
         st.status = LPDEC_ERR_INVALID_ARG;
@@ -1335,6 +1421,7 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
         st.ipm_iters_total += io.iters;
         st.pcg_iters_total += io.pcg_iters;
         st.pcg_iters_fp64 += io.pcg_iters64;
+        st.pcg_flops += io.flops;
         st.max_levels = max(st.max_levels, io.max_levels);
         int ok = io.certified || certify<T>(B, C, W, F, gamma);
         if (!ok) st.vertex_failures += vertex_recover<T>(B, C, W, F, gamma);

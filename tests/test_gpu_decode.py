@@ -78,12 +78,17 @@ def test_decode_edge_cases():
         g = np.abs(awgn_llr_frames(code.n, code.design_rate, 2.0, 0, [0])) + 0.25
         u, hard, cert, masks, st = d.decode_batch(g)
         assert st["alp_iters"][0] == 0 and cert[0] == 1 and not hard.any() and not masks.any()
-        # zero LLRs are allowed (treated as gamma >= 0)
+        # zero LLRs are accepted (treated as gamma >= 0). The LP optimum need
+        # not be unique then and Theorem 2 (strictly increasing cost, hence
+        # termination) assumes it is, so the decoder only owes a defined
+        # status, and the oracle's optimal cost whenever both converge.
         g0 = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, [1])
         g0[0, ::7] = 0.0
         u, hard, cert, masks, st = d.decode_batch(g0)
         res = oracle.decode(code, g0[0])
-        assert cert[0] == res.cert and st["status"][0] == 0
+        assert st["status"][0] in (L.LPDEC_OK, L.LPDEC_ERR_NOT_CONVERGED)
+        if st["status"][0] == 0 and res.status == 0:
+            assert abs(st["objective"][0] - res.objective) <= 1e-6 * (1 + abs(res.objective))
         # non-finite LLRs: host entry rejects the call
         bad = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, [2])
         bad[0, 5] = np.nan
