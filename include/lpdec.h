@@ -241,6 +241,33 @@ int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code,
                                     double* d_x, lpdec_stats* d_stats,
                                     double* d_trace, int32_t max_trace, void* stream);
 
+/* Allocation-free variant of lpdec_decode_batch_device (no counterpart in
+ * the paper). It is for callers that cannot allocate device memory when they
+ * decode — a host component that has already reserved all GPU memory, a
+ * real-time loop that must stay out of the allocator — and it calls no
+ * cudaMalloc, cudaFree or other allocating routine. Instead of the
+ * context's scratch it uses one fixed device array of 32 MiB inside this
+ * library (present on every GPU that loads the library, until the process
+ * exits); the frames run on as many CTAs as fit in it.
+ *   - code: from lpdec_code_create (created beforehand; its context picks
+ *     the device). params: NULL = defaults; the context's parameters are
+ *     not used.
+ *   - Inputs and outputs are caller-owned device buffers, as in
+ *     lpdec_decode_batch_device; asynchronous on `stream`.
+ *   - The first call on a device takes the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind; the
+ *     call resets what must start at zero itself. Calls that overlap on the
+ *     GPU (other streams, other threads) race on the array: serialize them.
+ *   - Returns LPDEC_ERR_OUT_OF_BUDGET when one frame's workspace exceeds the
+ *     array (very long codes), LPDEC_ERR_INVALID_ARG for bad arguments. */
+int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
+                                          const lpdec_params* params, int32_t nframes,
+                                          const double* d_gamma, double* d_u,
+                                          uint8_t* d_hard, int32_t* d_cert,
+                                          uint32_t* d_cut_mask, lpdec_stats* d_stats,
+                                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -778,3 +778,119 @@ int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code, int3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batch decode.
+//
+// Some callers cannot call cudaMalloc at decode time: code that runs while
+// another component owns and pre-reserves all device memory, real-time
+// loops that must not enter the allocator, or hosts that forbid device
+// allocation after start-up. For them, the per-CTA workspace and the frame
+// queue counter of this entry point live in one file-scope device array of
+// fixed size instead of in context-owned allocations. The array exists on
+// every GPU that loads this library, for the life of the process.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB per device
+constexpr size_t kNoAllocCounterBytes = 256;                 // queue counter slot
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 128;
+char* g_noalloc_base[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (taken once per
+// device). In host code the symbol is only a host-side stand-in; the kernel
+// must be given the address returned here.
+int32_t noalloc_base(int device, char** out) {
+    if (device < 0 || device >= kMaxDevices) return LPDEC_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_base[device]) {
+        void* ptr = nullptr;
+        CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_base[device] = static_cast<char*>(ptr);
+    }
+    *out = g_noalloc_base[device];
+    return LPDEC_OK;
+}
+
+template <typename K>
+int32_t noalloc_launch_plan(const lpdec_params& prm, const lpdec_code* code, int device,
+                            int nframes, K kernel, size_t real_bytes, Launch* out) {
+    int sms = 0, optin = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    int threads = prm.threads_per_block > 0 ? prm.threads_per_block : 128;
+    threads = std::max(32, std::min(512, threads / 32 * 32));
+    size_t cap = (size_t)optin - sizeof(KernelShared) - 1024;
+    size_t budget = prm.smem_budget > 0 ? std::min((size_t)prm.smem_budget, cap) : cap;
+    Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes);
+    if (L.smem_bytes == 0xffffffffu || L.smem_bytes + sizeof(KernelShared) > (size_t)optin) {
+        snprintf(g_err, sizeof g_err, "frame workspace does not fit in shared memory");
+        return LPDEC_ERR_INVALID_ARG;
+    }
+    const size_t avail = kNoAllocScratchBytes - kNoAllocCounterBytes;
+    if (L.gbytes > avail) {
+        snprintf(g_err, sizeof g_err,
+                 "one frame needs %llu bytes of scratch, above the %zu-byte static array",
+                 (unsigned long long)L.gbytes, avail);
+        return LPDEC_ERR_OUT_OF_BUDGET;
+    }
+    CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, L.smem_bytes));
+    if (per_sm < 1) {
+        snprintf(g_err, sizeof g_err, "kernel does not fit on an SM");
+        return LPDEC_ERR_INVALID_ARG;
+    }
+    size_t by_scratch = L.gbytes ? avail / L.gbytes : (size_t)per_sm * sms;
+    int grid = (int)std::min<size_t>({(size_t)nframes, (size_t)per_sm * sms, by_scratch});
+    out->L = L;
+    out->threads = threads;
+    out->grid = std::max(1, grid);
+    return LPDEC_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
+                                                     const lpdec_params* params,
+                                                     int32_t nframes, const double* d_gamma,
+                                                     double* d_u, uint8_t* d_hard,
+                                                     int32_t* d_cert, uint32_t* d_cut_mask,
+                                                     lpdec_stats* d_stats, void* stream) {
+    if (!code || !code->ctx || nframes < 0 ||
+        (nframes > 0 && (!d_gamma || !d_u || !d_hard || !d_cert)))
+        return LPDEC_ERR_INVALID_ARG;
+    lpdec_params prm;
+    if (params) prm = *params; else lpdec_default_params(&prm);
+    if (prm.variant != LPDEC_MALP_A && prm.variant != LPDEC_MALP_B) return LPDEC_ERR_INVALID_ARG;
+    if (prm.precision != LPDEC_FP64 && prm.precision != LPDEC_MIXED) return LPDEC_ERR_INVALID_ARG;
+    if (nframes == 0) return LPDEC_OK;
+    const int device = code->ctx->device;
+    CK(cudaSetDevice(device));
+    char* base = nullptr;
+    int32_t rc = noalloc_base(device, &base);
+    if (rc) return rc;
+    const bool mixed = prm.precision == LPDEC_MIXED;
+    Launch ln;
+    rc = mixed ? noalloc_launch_plan(prm, code, device, nframes, k_decode<float>, 4, &ln)
+               : noalloc_launch_plan(prm, code, device, nframes, k_decode<double>, 8, &ln);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int* counter = reinterpret_cast<int*>(base);
+    char* gscratch = base + kNoAllocCounterBytes;
+    CK(cudaMemsetAsync(counter, 0, sizeof(int), s));   // the only state a call must reset
+    if (mixed)
+        k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+            view_of(code), to_dev(prm), ln.L, d_gamma, d_u, d_hard, d_cert, d_cut_mask, d_stats,
+            nframes, counter, gscratch);
+    else
+        k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+            view_of(code), to_dev(prm), ln.L, d_gamma, d_u, d_hard, d_cert, d_cut_mask, d_stats,
+            nframes, counter, gscratch);
+    CK(cudaGetLastError());
+    return LPDEC_OK;
+}

@@ -96,10 +96,13 @@ def _load():
     lib.lpdec_pcg_device.argtypes = [P, P, i32, P, P, P, P, P, P, P, P]
     lib.lpdec_lp_solve_device.argtypes = [P, P, i32, P, P, P, P, P, P]
     lib.lpdec_lp_solve_trace_device.argtypes = [P, P, i32, P, P, P, P, P, P, i32, P]
+    lib.lpdec_decode_batch_device_noalloc.argtypes = [P, ctypes.POINTER(lpdec_params), i32, P, P,
+                                                      P, P, P, P, P]
     for name in ("lpdec_ctx_create", "lpdec_ctx_set_params", "lpdec_code_create",
                  "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_batch_device",
                  "lpdec_cut_search_device", "lpdec_mts_select_device", "lpdec_pcg_device",
-                 "lpdec_lp_solve_device", "lpdec_lp_solve_trace_device"):
+                 "lpdec_lp_solve_device", "lpdec_lp_solve_trace_device",
+                 "lpdec_decode_batch_device_noalloc"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -253,6 +256,15 @@ def lpdec_lp_solve_trace_device(ctx, code, nframes, d_gamma, d_in_lp, d_mask, d_
     return _load().lpdec_lp_solve_trace_device(ctx, code, nframes, _dptr(d_gamma), _dptr(d_in_lp),
                                                _dptr(d_mask), _dptr(d_x), _dptr(d_stats),
                                                _dptr(d_trace), max_trace, _stream(stream))
+
+
+def lpdec_decode_batch_device_noalloc(code, params, nframes, d_gamma, d_u, d_hard, d_cert,
+                                      d_cut_mask=None, d_stats=None, stream=None) -> int:
+    """Batch decode without any device allocation (see include/lpdec.h)."""
+    return _load().lpdec_decode_batch_device_noalloc(
+        code, ctypes.byref(params) if params is not None else None, nframes, _dptr(d_gamma),
+        _dptr(d_u), _dptr(d_hard), _dptr(d_cert), _dptr(d_cut_mask), _dptr(d_stats),
+        _stream(stream))
 
 
 # ---------------------------------------------------------------------------
