@@ -47,6 +47,6 @@ class OracleParams:
     tau_cut: float = 1e-9
     tau_int: float = 1e-9
     max_alp: int = 200
-    max_ipm: int = 200
+    max_ipm: int = 60
     max_pcg: int = 1000
     variant: str = "malp_a"   # "malp_a" | "malp_b" | "alp"

@@ -441,7 +441,7 @@ void lpdec_default_params(lpdec_params* p) {
     p->tol_feas_loose = 1e-6;
     p->tol_cert = 1e-3;
     p->max_alp = 200;
-    p->max_ipm = 200;
+    p->max_ipm = 60;
     p->max_pcg = 2000;
     p->variant = LPDEC_MALP_A;
     p->precision = LPDEC_FP64;

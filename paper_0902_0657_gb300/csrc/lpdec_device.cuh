@@ -1140,11 +1140,11 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
     for (int it = 0;; ++it) {
         // Expensive regime (the basis certificate keeps failing and Newton
         // solves need hundreds of PCG iterations, typical of LPs with a
-        // fractional optimum): once the gap is small and the partition
+        // fractional optimum): below gap tol_cert, whenever the partition
         // x_i > z_i has not moved for an iteration, try the general
         // certificate (CG on the basic columns), far cheaper than one more
         // interior-point iteration here.
-        if (prev_grel < 1e-5 && last_pcg > 200) {
+        if (prev_grel < P.tol_cert && last_pcg > 200) {
             double c0 = 0.0, c1 = 0.0;
             for (int i = B.tid; i < q; i += B.nt)
                 if (W.x[i] > W.zz[i]) { c0 += 1.0; c1 += (double)(i + 1) * (double)(i + 1); }
@@ -1392,9 +1392,16 @@ struct FrameOut {
     lpdec_stats* stats; // may be null
 };
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <typename T>
 __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const DevParams& P,
                                     const double* gamma, FrameOut out, int q2, int* shscan) {
+    const unsigned long long t0 = global_ns();
     int bad = 0;
     for (int i = B.tid; i < C.n; i += B.nt) bad |= !isfinite(gamma[i]);
     bad = __syncthreads_or(bad);
@@ -1450,6 +1457,7 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
         *out.cert = frac ? 0 : 1;
         st.status = status;
         st.objective = obj;
+        st.seconds = 1e-9 * (double)(global_ns() - t0);
         if (out.stats) *out.stats = st;
     }
     __syncthreads();
