@@ -53,9 +53,15 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--frames", type=int, default=20000, help="frames per step per GPU")
+    ap.add_argument("--frames", type=int, default=20000, help="frames per timed step per GPU")
+    ap.add_argument("--warmup-frames", type=int, default=152,
+                    help="frames per warm-up step (same kernel and code, fewer frames)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--threads", type=int, default=128)
+    ap.add_argument("--smem-budget", type=int, default=0,
+                    help="shared-memory bytes per CTA (0 = library choice)")
+    ap.add_argument("--ebn0", type=float, default=EBN0_DB,
+                    help="Eb/N0 in dB (2.0 is the workload; other values for small profiling cases)")
     ap.add_argument("--oracle-seconds", type=float, default=15.0,
                     help="CPU seconds per oracle worker for the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -65,18 +71,29 @@ def parse_args():
 
 def workload_config(args, n, m):
     return {
-        "workload": f"(3,6) PEG LDPC n={n} m={m}, BPSK/AWGN Eb/N0 {EBN0_DB} dB, all-zero codeword, "
+        "workload": f"(3,6) PEG LDPC n={n} m={m}, BPSK/AWGN Eb/N0 {args.ebn0} dB, all-zero codeword, "
                     f"{POOL}-frame pool (seed {SEED}), {args.frames} frames per step per GPU",
-        "code": CODE_NAME, "n": n, "m": m, "ebn0_db": EBN0_DB, "pool_frames": POOL,
-        "frames_per_step": args.frames, "precision": args.precision,
+        "code": CODE_NAME, "n": n, "m": m, "ebn0_db": args.ebn0, "pool_frames": POOL,
+        "frames_per_step": args.frames, "warmup_frames_per_step": args.warmup_frames,
+        "precision": args.precision, "smem_budget": args.smem_budget or "library (1/3 of SM)",
         "threads_per_block": args.threads, "variant": "MALP-A",
         "l2": "flushed by a 256 MB write between timed steps",
     }
 
 
 def frame_ids(step, rank, world, per_step):
+    """Frames of one rank in one step: the ranks of a step take consecutive,
+    disjoint blocks of the pool (weak scaling, no exchange between ranks)."""
     base = (step * world + rank) * per_step
     return [(base + i) % POOL for i in range(per_step)]
+
+
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (a plain float on one rank)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ---------------------------------------------------------------------------
@@ -84,7 +101,7 @@ def frame_ids(step, rank, world, per_step):
 # ---------------------------------------------------------------------------
 
 def _oracle_worker(args):
-    wid, nworkers, seconds, frames = args
+    wid, nworkers, seconds, frames, ebn0 = args
     import numpy as np  # noqa: F401
     import oracle
     from synth import awgn_llr_frames, named_code
@@ -92,7 +109,7 @@ def _oracle_worker(args):
     t0 = time.perf_counter()
     done = 0
     for f in frames[wid::nworkers]:
-        g = awgn_llr_frames(code.n, code.design_rate, EBN0_DB, SEED, [f])[0]
+        g = awgn_llr_frames(code.n, code.design_rate, ebn0, SEED, [f])[0]
         oracle.decode(code, g)
         done += 1
         if time.perf_counter() - t0 >= seconds:
@@ -100,14 +117,14 @@ def _oracle_worker(args):
     return done, time.perf_counter() - t0
 
 
-def run_oracle_sample(seconds, offset):
+def run_oracle_sample(seconds, offset, ebn0):
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
     cores = os.cpu_count() or 1
     frames = [(offset + i) % POOL for i in range(10 * cores)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_worker, [(w, cores, seconds, frames) for w in range(cores)])
+        res = pool.map(_oracle_worker, [(w, cores, seconds, frames, ebn0) for w in range(cores)])
     done = sum(r[0] for r in res)
     wall = max(r[1] for r in res)
     return done, wall, cores
@@ -195,11 +212,13 @@ def run_ours(args):
     prm = L.lpdec_default_params()
     prm.precision = L.LPDEC_MIXED if args.precision == "mixed" else L.LPDEC_FP64
     prm.threads_per_block = args.threads
+    prm.smem_budget = args.smem_budget
     dec = L.Decoder(code, device=local, params=prm)
 
     nsteps = args.warmup + args.steps
-    gam = [torch.from_numpy(awgn_llr_frames(n, code.design_rate, EBN0_DB, SEED,
-                                            frame_ids(k, rank, world, B_))).cuda()
+    sizes = [min(args.warmup_frames, B_) if k < args.warmup else B_ for k in range(nsteps)]
+    gam = [torch.from_numpy(awgn_llr_frames(n, code.design_rate, args.ebn0, SEED,
+                                            frame_ids(k, rank, world, sizes[k]))).cuda()
            for k in range(nsteps)]
     d_u = torch.empty((B_, n), dtype=torch.float64, device="cuda")
     d_h = torch.empty((B_, n), dtype=torch.uint8, device="cuda")
@@ -210,8 +229,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step(k):
-        rc = L.lpdec_decode_batch_device(dec.ctx, dec.code, B_, gam[k], d_u, d_h, d_c, d_m, d_s,
-                                         stream=stream)
+        rc = L.lpdec_decode_batch_device(dec.ctx, dec.code, sizes[k], gam[k], d_u, d_h, d_c, d_m,
+                                         d_s, stream=stream)
         if rc != 0:
             raise RuntimeError(f"decode failed: {L.error_string(rc)}")
 
@@ -219,7 +238,7 @@ def run_ours(args):
         step(k)
     torch.cuda.synchronize()
 
-    times, flops, stats_all = [], 0.0, []
+    times, flops, stats_all, certs_all = [], 0.0, [], []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -236,17 +255,14 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1) / 1e3)
             st = d_s.cpu().numpy().view(L.STATS_DTYPE)
             stats_all.append(st.copy())
+            certs_all.append(d_c.cpu().numpy().copy())
             flops += float(st["pcg_flops"].sum())
         torch.cuda.synchronize()
         wall = time.perf_counter() - t_wall0
     if world > 1:
         dist.barrier()
     t_total = sum(times)
-    t_max = t_total
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_total, dist, "cuda") if world > 1 else t_total
     frames_total = B_ * args.steps * world
     value = frames_total / t_max
 
@@ -269,9 +285,7 @@ def run_ours(args):
         if rc != 0:
             raise RuntimeError(f"host decode failed: {L.error_string(rc)}")
         if world > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+            te = max_over_ranks(te, dist, "cuda")
         e2e = {"value": B_ * world / te, "unit": UNIT, "h2d_bytes_per_step": B_ * n * 8,
                "d2h_bytes_per_step": B_ * (n * 8 + n + 4 + m * 4 + L.STATS_DTYPE.itemsize)}
 
@@ -293,7 +307,7 @@ def run_ours(args):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        done, w, cores = run_oracle_sample(args.oracle_seconds, offset=0)
+        done, w, cores = run_oracle_sample(args.oracle_seconds, offset=0, ebn0=args.ebn0)
         cpu = {"value": done / w, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{done} frames of the same workload (pool frames from 0), "
                          f"{cores} spawned single-threaded workers, ~{args.oracle_seconds:.0f} s each"}
@@ -311,8 +325,10 @@ def run_ours(args):
                        "max": 1e3 * float(st["seconds"].max()),
                        "what": "device time of one frame on its CTA inside the batch"},
         "detail": {
-            "frames_integral": float((st["status"] == 0).mean()) if st.size else None,
-            "frames_not_converged": int((st["status"] != 0).sum()),
+            "frames_integral": float((np.concatenate(certs_all) == 1).mean()),
+            "frames_ok": int((st["status"] == L.LPDEC_OK).sum()),
+            "frames_stalled": int((st["status"] == L.LPDEC_ERR_STALLED).sum()),
+            "frames_not_converged": int((st["status"] == L.LPDEC_ERR_NOT_CONVERGED).sum()),
             "mean_lps_per_frame": float(st["alp_iters"].mean()),
             "mean_ipm_iters_per_frame": float(st["ipm_iters_total"].mean()),
             "mean_pcg_iters_per_frame": float(st["pcg_iters_total"].mean()),
@@ -339,7 +355,7 @@ def run_reference(args):
     code = named_code(CODE_NAME)
     total_done, total_wall, cores = 0, 0.0, 1
     for k in range(args.warmup + args.steps):
-        done, w, cores = run_oracle_sample(args.oracle_seconds, offset=k * 997)
+        done, w, cores = run_oracle_sample(args.oracle_seconds, offset=k * 997, ebn0=args.ebn0)
         if k >= args.warmup:
             total_done += done
             total_wall += w

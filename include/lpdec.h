@@ -54,6 +54,7 @@ extern "C" {
 #define LPDEC_ERR_PENDING       -5  /* result not ready yet */
 #define LPDEC_ERR_CUDA          -6  /* a CUDA runtime call failed */
 #define LPDEC_ERR_NO_DEVICE     -7  /* no CUDA device / unsupported architecture */
+#define LPDEC_ERR_STALLED       -8  /* the LP cost stopped rising (per frame; see tau_inc) */
 
 /* Adaptive-LP variants (Section III-A). */
 #define LPDEC_MALP_A 0
@@ -84,6 +85,13 @@ extern "C" {
  *   tau_act  = 1e-9   an inequality is active iff its slack <= tau_act
  *   tau_cut  = 1e-9   a check is violated iff Eq. 6's left side < 1 - tau_cut
  *   tau_int  = 1e-9   u is integral iff max |u_i - round(u_i)| <= tau_int
+ *   tau_inc  = 1e-9   Theorem 2(b): with unique LP optima the cost gamma'u
+ *                     rises strictly from LP to LP. A frame whose new LP cost
+ *                     is not above the previous one by more than
+ *                     tau_inc * (1 + |previous|) ends with LPDEC_ERR_STALLED
+ *                     (an optimum that is not unique, where the adaptive loop
+ *                     can cycle between two cut sets), keeping the last LP's
+ *                     solution.
  *   max_alp = 200, max_ipm = 60, max_pcg = 2000 iteration caps (max_pcg per
  *                     Newton solve, over all refinement rounds; an LP whose
  *                     interior-point run converges needs at most ~40
@@ -100,6 +108,7 @@ typedef struct lpdec_params {
     double tol_inner;       /* relative tolerance of one FP32 PCG round (LPDEC_MIXED) */
     double tol_feas_loose;  /* infeasibility accepted once the gap is below tol_gap */
     double tol_cert;        /* gap below which the optimality certificate is tried */
+    double tau_inc;         /* least relative cost rise from one LP to the next */
     int32_t max_alp, max_ipm, max_pcg, variant, precision;
     int32_t threads_per_block;  /* 0 = library choice */
     int32_t smem_budget;        /* bytes of shared memory per CTA, 0 = library choice */
@@ -108,7 +117,7 @@ typedef struct lpdec_params {
 
 /* Per-frame results besides u / hard / cert. */
 typedef struct lpdec_stats {
-    int32_t status;           /* LPDEC_OK or LPDEC_ERR_NOT_CONVERGED / INVALID_ARG */
+    int32_t status;           /* LPDEC_OK, or LPDEC_ERR_NOT_CONVERGED / STALLED / INVALID_ARG */
     int32_t alp_iters;        /* number of LPs solved (0 if the hard decision is a codeword) */
     int32_t ipm_iters_total;  /* interior-point iterations over all LPs */
     int32_t pcg_iters_total;  /* PCG iterations over all Newton steps */

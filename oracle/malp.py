@@ -10,6 +10,10 @@ MALP-A (Section III-A):
      inequality, drop j's old (inactive) inequality, if any, and add the new
      one. If anything was added, solve the LP to get u^k. Stop when nothing
      was added; u^k is the LP decoding solution.
+  Theorem 2(b) makes the cost gamma'u^k strictly increasing when every LP
+  optimum is unique; a cost that does not rise (by more than tau_inc,
+  relative) ends the frame with status STALLED instead of letting the loop
+  cycle between cut sets.
   MALP-B moves the removal to the start of the round: every inactive
   inequality is dropped before the search. ALP never removes anything and
   searches every check.
@@ -38,7 +42,7 @@ from . import cuts as _cuts
 from . import ipm as _ipm
 from . import lp as _lp
 from . import vertex as _vertex
-from .params import OracleParams, OK, NOT_CONVERGED
+from .params import OracleParams, OK, NOT_CONVERGED, STALLED
 
 
 @dataclasses.dataclass
@@ -92,6 +96,7 @@ def decode(code, gamma, params: OracleParams | None = None,
     gamma = np.asarray(gamma, dtype=np.float64)
     n, m = code.n, code.m
     u = hard_decision(gamma)
+    cost = float(np.dot(gamma, u))      # gamma'u^0
     in_lp = np.zeros(m, dtype=bool)
     masks = np.zeros(m, dtype=np.uint32)
     slack = np.full(m, np.inf)         # slack of check j's inequality
@@ -151,6 +156,11 @@ def decode(code, gamma, params: OracleParams | None = None,
         if res.status != OK:
             status = NOT_CONVERGED
             break
+        new_cost = history[-1].objective
+        if new_cost - cost <= prm.tau_inc * (1.0 + abs(cost)):
+            status = STALLED
+            break
+        cost = new_cost
     hard, cert = outputs(u, gamma, prm.tau_int)
     out_masks = np.where(in_lp, masks, 0).astype(np.uint32)
     final_cuts = alp_cuts if prm.variant == "alp" else \

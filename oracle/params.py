@@ -22,6 +22,13 @@ tests pass identical values to both sides explicitly.
   tau_cut   check j is violated iff the left side of Eq. 6 for the set V of
             Algorithm 2 is < 1 - tau_cut.
   tau_int   the output is integral iff max_i |u_i - round(u_i)| <= tau_int.
+  tau_inc   Theorem 2(b): with unique LP optima the cost gamma'u^k rises
+            strictly from one LP to the next, so no cut set repeats. When
+            an LP's cost does not exceed the previous one by more than
+            tau_inc * (1 + |previous cost|), that hypothesis has failed (a
+            tie or a numerically non-unique optimum, where MALP can cycle
+            between two cut sets) and the frame ends with status STALLED,
+            keeping the last LP's solution.
   max_alp, max_ipm, max_pcg: iteration caps; reaching one ends the frame
             with status NOT_CONVERGED.
 """
@@ -33,6 +40,7 @@ import dataclasses
 # frame status codes (same values as the C library's LPDEC_* codes)
 OK = 0
 NOT_CONVERGED = -3
+STALLED = -8
 
 
 @dataclasses.dataclass
@@ -46,6 +54,7 @@ class OracleParams:
     tau_act: float = 1e-9
     tau_cut: float = 1e-9
     tau_int: float = 1e-9
+    tau_inc: float = 1e-9
     max_alp: int = 200
     max_ipm: int = 60
     max_pcg: int = 1000

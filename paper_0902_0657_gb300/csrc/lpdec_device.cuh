@@ -39,7 +39,7 @@ struct CodeView {
 
 struct DevParams {
     double sigma, eta, tol_gap, tol_feas, tol_pcg, tau_act, tau_cut, tau_int;
-    double pcg_gap_factor, tol_inner, tol_feas_loose, tol_cert;
+    double pcg_gap_factor, tol_inner, tol_feas_loose, tol_cert, tau_inc;
     int max_alp, max_ipm, max_pcg, variant, precision;
 };
 
@@ -1392,6 +1392,14 @@ struct FrameOut {
     lpdec_stats* stats; // may be null
 };
 
+// gamma'u over the frame (the same value in every thread).
+template <typename T>
+__device__ inline double frame_cost(Blk& B, const CodeView& C, WS<T>& W, const double* gamma) {
+    double a = 0.0;
+    for (int i = B.tid; i < C.n; i += B.nt) a += gamma[i] * W.u[i];
+    return bsum(B, a);
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1417,6 +1425,7 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
     }
     frame_init<T>(B, C, W, gamma);
     int status = LPDEC_OK;
+    double cost = frame_cost(B, C, W, gamma);    // gamma'u^0
     for (;;) {
         if (P.variant == LPDEC_MALP_B) drop_inactive<T>(B, C, W);
         int added = cut_search<T>(B, C, W, P);
@@ -1435,6 +1444,11 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
         lp_finish<T>(B, C, W, F, P);
         st.lp_rows_final = F.p;
         if (!io.converged && !ok) { status = LPDEC_ERR_NOT_CONVERGED; break; }
+        // Theorem 2(b): with unique LP optima the cost rises strictly; a
+        // cost that does not rise means the loop may cycle between cut sets.
+        const double next = frame_cost(B, C, W, gamma);
+        if (next - cost <= P.tau_inc * (1.0 + fabs(cost))) { status = LPDEC_ERR_STALLED; break; }
+        cost = next;
     }
     // a7: outputs. cert = integral; hard_i = [u_i > 1/2], the channel's
     // decision where u_i is within tau_int of 1/2.

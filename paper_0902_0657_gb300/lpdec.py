@@ -24,6 +24,7 @@ LPDEC_ERR_TIMEOUT = -4
 LPDEC_ERR_PENDING = -5
 LPDEC_ERR_CUDA = -6
 LPDEC_ERR_NO_DEVICE = -7
+LPDEC_ERR_STALLED = -8
 LPDEC_MALP_A = 0
 LPDEC_MALP_B = 1
 LPDEC_FP64 = 0
@@ -33,7 +34,7 @@ LPDEC_MIXED = 1
 class lpdec_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("sigma", "eta", "tol_gap", "tol_feas", "tol_pcg", "tau_act", "tau_cut", "tau_int",
-                 "pcg_gap_factor", "tol_inner", "tol_feas_loose", "tol_cert")] + \
+                 "pcg_gap_factor", "tol_inner", "tol_feas_loose", "tol_cert", "tau_inc")] + \
                [(k, ctypes.c_int32) for k in
                 ("max_alp", "max_ipm", "max_pcg", "variant", "precision",
                  "threads_per_block", "smem_budget", "reserved")]

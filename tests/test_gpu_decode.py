@@ -86,7 +86,7 @@ def test_decode_edge_cases():
         g0[0, ::7] = 0.0
         u, hard, cert, masks, st = d.decode_batch(g0)
         res = oracle.decode(code, g0[0])
-        assert st["status"][0] in (L.LPDEC_OK, L.LPDEC_ERR_NOT_CONVERGED)
+        assert st["status"][0] in (L.LPDEC_OK, L.LPDEC_ERR_NOT_CONVERGED, L.LPDEC_ERR_STALLED)
         if st["status"][0] == 0 and res.status == 0:
             assert abs(st["objective"][0] - res.objective) <= 1e-6 * (1 + abs(res.objective))
         # non-finite LLRs: host entry rejects the call
@@ -139,3 +139,21 @@ def test_code_create_validates_csr():
             L.lpdec_code_create(ctx, 1, 40, rp33, np.arange(33, dtype=np.int32))
     finally:
         L.lpdec_ctx_destroy(ctx)
+
+
+def test_stall_rule_matches_oracle():
+    """Theorem 2(b) stop rule: with a required cost rise larger than any
+    real one, every frame that needs an LP stops after its first LP with
+    LPDEC_ERR_STALLED, and its outputs are that LP's, as in the oracle."""
+    from oracle.params import OracleParams
+    torch_cuda()
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(32))
+    prm = L.lpdec_default_params()
+    prm.tau_inc = 1e6
+    with L.Decoder(code, params=prm) as d:
+        u, hard, cert, masks, st = d.decode_batch(G)
+    for f in range(32):
+        res = oracle.decode(code, G[f], OracleParams(tau_inc=1e6))
+        compare_frame(res, u[f], hard[f], cert[f], masks[f], st[f], f"frame {f}")
+        assert res.alp_iters == 0 or (res.status == L.LPDEC_ERR_STALLED and res.alp_iters == 1)

@@ -168,3 +168,25 @@ def test_initial_lp_is_hard_decision_and_codeword_input():
     res = oracle.decode(code, g)
     assert res.alp_iters == 0 and res.cert == 1
     assert np.all(res.u == 0) and np.all(res.hard == 0)
+
+
+def test_stall_rule_follows_theorem_2b():
+    """Theorem 2(b): the LP cost rises strictly from one LP to the next. A
+    required rise larger than any real one stops the frame right after its
+    first LP with status STALLED and that LP's solution; the default
+    tau_inc never stops a frame of the n=120 workload."""
+    from oracle.params import STALLED
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(40))
+    needs_lp = []
+    for g in G:
+        r = oracle.decode(code, g)
+        assert r.status == 0
+        costs = [float(np.dot(g, oracle.malp.hard_decision(g)))] + [h.objective for h in r.history]
+        assert all(b > a for a, b in zip(costs, costs[1:]))
+        if r.alp_iters > 1:
+            needs_lp.append(g)
+    assert needs_lp
+    r = oracle.decode(code, needs_lp[0], OracleParams(tau_inc=1e6))
+    assert r.status == STALLED and r.alp_iters == 1
+    assert np.array_equal(r.u, r.history[0].u)
