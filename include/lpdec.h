@@ -63,6 +63,9 @@ extern "C" {
 /* Arithmetic of the PCG solve (the IPM state is always FP64). */
 #define LPDEC_FP64  0   /* FP64 PCG */
 #define LPDEC_MIXED 1   /* FP32 PCG inner solves refined against FP64 residuals */
+#define LPDEC_M32   2   /* FP64 PCG whose preconditioner solve (the two triangular
+                           sweeps of Section V) runs in FP32; flexible direction
+                           update (Polak-Ribiere) */
 
 /*
  * Tolerances and rules the paper leaves open (its Section VII lists the

@@ -25,7 +25,19 @@ struct KernelShared {
     double red[128];
     int shscan[40];
     int next;
+    int sw;
 };
+
+// The warp of this CTA that runs its single-warp phases. A CTA's warps take
+// consecutive warp slots of its SM and a slot's sub-partition is its index
+// mod 4, so warp 0 of every CTA would share one sub-partition (and its FP64
+// pipe); rotating by the CTA's slot block spreads them. The choice affects
+// only where the work runs, never its result.
+__device__ __forceinline__ int serial_warp(int nwarps) {
+    unsigned slot;
+    asm volatile("mov.u32 %0, %%warpid;" : "=r"(slot));
+    return (int)((slot / (unsigned)nwarps) % (unsigned)nwarps);
+}
 
 __device__ __forceinline__ int next_frame(Blk& B, int* counter, int* slot) {
     if (B.tid == 0) *slot = atomicAdd(counter, 1);
@@ -39,7 +51,10 @@ __device__ __forceinline__ int next_frame(Blk& B, int* counter, int* slot) {
     extern __shared__ __align__(16) char smem[];                                \
     __shared__ KernelShared ks;                                                 \
     Blk B{(int)threadIdx.x, (int)blockDim.x, (int)(threadIdx.x & 31),          \
-          (int)(threadIdx.x >> 5), (int)(blockDim.x >> 5), ks.red, 0};          \
+          (int)(threadIdx.x >> 5), (int)(blockDim.x >> 5), ks.red, 0, 0};       \
+    if (threadIdx.x == 0) ks.sw = serial_warp(B.nwarps);                        \
+    __syncthreads();                                                            \
+    B.sw = ks.sw;                                                               \
     WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.gbytes, C0.n, C0.m,      \
                          (int)L.q2);                                            \
     const CodeView C = bind_code<T>(C0, W);
@@ -292,22 +307,27 @@ bool layout_ok(const Layout& L, const std::vector<size_t>& sizes) {
 // budget; the bitmap and the level pointer arrays, which the kernels update
 // with shared-memory atomics, always do. The FP64 interior-point state goes
 // to per-CTA global scratch.
-Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes) {
+Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes, bool m32) {
     const size_t q = (size_t)n + m;
     size_t q2 = 1;
     while (q2 < q) q2 <<= 1;
-    const size_t vec = std::max(real_bytes * vec_elems(n, m), 8 * q2 + 4 * q);
+    const size_t vec = std::max(vec_bytes(n, m, real_bytes, m32), 8 * q2 + 4 * q);
     struct Spec { int id; size_t bytes; int where; };  // 0 = budgeted, 1 = always shared, 2 = global
     const size_t D = 8, I = 4, H = 2;
     std::vector<Spec> specs = {
         {S_BITMAP, I * ((q + 31) / 32), 1}, {S_LBPTR, I * (m + 2), 1}, {S_LFPTR, I * (m + 2), 1},
         {S_CUR, I * (m + 2), 1},
-        {S_VEC, vec, 0}, {S_ROWENT, H * E, 0}, {S_COLENT, H * E, 0}, {S_PIVROW, H * q, 0},
-        {S_PIVCOL, H * m, 0}, {S_ROWCHK, H * m, 0}, {S_CHKROW, H * m, 0}, {S_PSGN, (size_t)m, 0},
-        {S_LBROWS, H * m, 0}, {S_LFROWS, H * m, 0}, {S_LB, H * m, 0}, {S_LF, H * m, 0},
-        {S_SELROW, H * m, 0}, {S_DEG, q, 0}, {S_FLAGS, (size_t)m, 0}, {S_MASK, I * m, 0},
-        {S_FLIP, I * ((n + 31) / 32), 0}, {S_HPTR, I * (m + 1), 0}, {S_VPTR, I * (n + 1), 0},
-        {S_BPTR, I * (m + 1), 0}, {S_FPTR, I * (m + 1), 0}, {S_BDEP, H * E, 0}, {S_FDEP, H * E, 0},
+        // budgeted arrays in priority order: first what every PCG iteration
+        // reads on its serial path (the two level-scheduled triangular
+        // solves), then the sparse passes of Q h, then what runs once per
+        // interior-point iteration (MTS selection, level build, cut search)
+        {S_VEC, vec, 0}, {S_BDEP, H * E, 0}, {S_FDEP, H * E, 0}, {S_BPTR, I * (m + 1), 0},
+        {S_FPTR, I * (m + 1), 0}, {S_LBROWS, H * m, 0}, {S_LFROWS, H * m, 0},
+        {S_PSGN, (size_t)m, 0}, {S_ROWENT, H * E, 0}, {S_ROWCHK, H * m, 0},
+        {S_HPTR, I * (m + 1), 0}, {S_COLENT, H * E, 0}, {S_VPTR, I * (n + 1), 0},
+        {S_PIVROW, H * q, 0}, {S_PIVCOL, H * m, 0}, {S_CHKROW, H * m, 0}, {S_LB, H * m, 0},
+        {S_LF, H * m, 0}, {S_SELROW, H * m, 0}, {S_DEG, q, 0}, {S_FLAGS, (size_t)m, 0},
+        {S_MASK, I * m, 0}, {S_FLIP, I * ((n + 31) / 32), 0},
         {G_X, D * q, 2}, {G_Z, D * q, 2}, {G_RC, D * q, 2}, {G_D2, D * q, 2}, {G_Y, D * m, 2},
         {G_B, D * m, 2}, {G_W, D * m, 2}, {G_DY, D * m, 2}, {G_R64, D * m, 2}, {G_U, D * n, 2},
         {G_T64, D * n, 2}, {G_BASIC, q, 2},
@@ -357,7 +377,8 @@ int32_t plan(lpdec_ctx* ctx, const lpdec_code* code, int nframes, K kernel, size
     const size_t per_cta = sizeof(KernelShared) + 1024 + 256;
     size_t budget = ctx->prm.smem_budget > 0 ? std::min((size_t)ctx->prm.smem_budget, cap)
                   : (third > per_cta ? std::min(cap, third - per_cta) : cap);
-    Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes);
+    Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes,
+                           ctx->prm.precision == LPDEC_M32);
     if (L.smem_bytes == 0xffffffffu) {
         snprintf(g_err, sizeof g_err, "inconsistent workspace layout");
         return LPDEC_ERR_INVALID_ARG;
@@ -477,10 +498,11 @@ int32_t lpdec_workspace_bytes(int32_t m, int32_t n, int32_t E, int32_t precision
                               int32_t smem_budget, size_t* smem_bytes,
                               size_t* global_bytes_per_frame) {
     if (m <= 0 || n <= 0 || m > 32767 || n > 32767 || E <= 0 || E > 32 * m ||
-        (precision != LPDEC_FP64 && precision != LPDEC_MIXED))
+        (precision != LPDEC_FP64 && precision != LPDEC_MIXED && precision != LPDEC_M32))
         return LPDEC_ERR_INVALID_ARG;
     size_t budget = smem_budget > 0 ? (size_t)smem_budget : (size_t)227 * 1024;
-    Layout L = make_layout(n, m, E, budget, precision == LPDEC_MIXED ? 4 : 8);
+    Layout L = make_layout(n, m, E, budget, precision == LPDEC_MIXED ? 4 : 8,
+                           precision == LPDEC_M32);
     if (L.smem_bytes == 0xffffffffu) return LPDEC_ERR_INVALID_ARG;
     if (smem_bytes) *smem_bytes = L.smem_bytes + sizeof(KernelShared);
     if (global_bytes_per_frame) *global_bytes_per_frame = (size_t)L.gbytes;
@@ -538,7 +560,9 @@ void lpdec_ctx_destroy(lpdec_ctx* ctx) {
 int32_t lpdec_ctx_set_params(lpdec_ctx* ctx, const lpdec_params* params) {
     if (!ctx || !params) return LPDEC_ERR_INVALID_ARG;
     if (params->variant != LPDEC_MALP_A && params->variant != LPDEC_MALP_B) return LPDEC_ERR_INVALID_ARG;
-    if (params->precision != LPDEC_FP64 && params->precision != LPDEC_MIXED) return LPDEC_ERR_INVALID_ARG;
+    if (params->precision != LPDEC_FP64 && params->precision != LPDEC_MIXED &&
+        params->precision != LPDEC_M32)
+        return LPDEC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->prm = *params;
     return LPDEC_OK;
@@ -839,7 +863,8 @@ int32_t noalloc_launch_plan(const lpdec_params& prm, const lpdec_code* code, int
     threads = std::max(32, std::min(512, threads / 32 * 32));
     size_t cap = (size_t)optin - sizeof(KernelShared) - 1024;
     size_t budget = prm.smem_budget > 0 ? std::min((size_t)prm.smem_budget, cap) : cap;
-    Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes);
+    Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes,
+                           prm.precision == LPDEC_M32);
     if (L.smem_bytes == 0xffffffffu || L.smem_bytes + sizeof(KernelShared) > (size_t)optin) {
         snprintf(g_err, sizeof g_err, "frame workspace does not fit in shared memory");
         return LPDEC_ERR_INVALID_ARG;
@@ -880,7 +905,8 @@ extern "C" int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
     lpdec_params prm;
     if (params) prm = *params; else lpdec_default_params(&prm);
     if (prm.variant != LPDEC_MALP_A && prm.variant != LPDEC_MALP_B) return LPDEC_ERR_INVALID_ARG;
-    if (prm.precision != LPDEC_FP64 && prm.precision != LPDEC_MIXED) return LPDEC_ERR_INVALID_ARG;
+    if (prm.precision != LPDEC_FP64 && prm.precision != LPDEC_MIXED && prm.precision != LPDEC_M32)
+        return LPDEC_ERR_INVALID_ARG;
     if (nframes == 0) return LPDEC_OK;
     const int device = code->ctx->device;
     CK(cudaSetDevice(device));

@@ -73,6 +73,12 @@ constexpr uint32_t kGlobalBit = 0x80000000u;
 __host__ __device__ constexpr size_t vec_elems(int n, int m) {
     return 7 * (size_t)m + 2 * (size_t)n;
 }
+// Bytes of the S_VEC block: the vectors above in type T and, for
+// LPDEC_M32, three FP32 vectors after them (the M-solve's right side and
+// solution, and 1/d^2 of the pivot columns).
+__host__ __device__ constexpr size_t vec_bytes(int n, int m, size_t real_bytes, bool m32) {
+    return real_bytes * vec_elems(n, m) + (m32 ? 12 * (size_t)m : 0);
+}
 
 struct Layout {
     uint32_t off[A_COUNT];     // byte offset; kGlobalBit set = global scratch
@@ -91,6 +97,7 @@ struct WS {
     uint16_t *bdep, *fdep;   // packed (row | kNeg): rows whose solved values row r needs
     uint8_t *psgn, *deg, *flags, *basic;
     T *xs, *r, *z, *h, *l, *t, *d2t, *invd2p;
+    float *rf, *zf, *ip32;      // FP32 M-solve vectors (LPDEC_M32 only)
     unsigned long long* skey;   // aliases the PCG vectors
     double *x, *zz, *rc, *d2, *y, *b, *w, *dy, *r64, *u, *t64;
     double *vx, *v1, *v2, *v3, *v4, *vr1, *vr2, *p64;
@@ -124,6 +131,7 @@ __device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws, int n, i
     w.sorted = w.rank + (n + m);
     w.xs = v; v += m; w.r = v; v += m; w.z = v; v += m; w.h = v; v += m; w.l = v; v += m;
     w.t = v; v += n; w.d2t = v; v += n + m; w.invd2p = v;
+    w.rf = reinterpret_cast<float*>(w.invd2p + m); w.zf = w.rf + m; w.ip32 = w.zf + m;
     P_(double, x, G_X); P_(double, zz, G_Z); P_(double, rc, G_RC); P_(double, d2, G_D2);
     P_(double, y, G_Y); P_(double, b, G_B); P_(double, w, G_W); P_(double, dy, G_DY);
     P_(double, r64, G_R64); P_(double, u, G_U); P_(double, t64, G_T64);
@@ -151,6 +159,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W, int n, int m) {
     double* q = W.p64;
     v.xs = q; q += m; v.r = q; q += m; v.z = q; q += m; v.h = q; q += m; v.l = q; q += m;
     v.t = q; q += n; v.invd2p = q;
+    v.rf = W.rf; v.zf = W.zf; v.ip32 = W.ip32;
     v.d2t = W.d2;
     v.skey = nullptr;
     v.x = W.x; v.zz = W.zz; v.rc = W.rc; v.d2 = W.d2; v.y = W.y; v.b = W.b; v.w = W.w;
@@ -180,6 +189,9 @@ struct Blk {
     int tid, nt, lane, warp, nwarps;
     double* red;   // shared [2][64]
     int phase;
+    int sw;        // the warp that runs the CTA's single-warp phases (level
+                   // sweeps, MTS greedy); rotated over the CTAs of an SM so
+                   // that their serial chains use different SM sub-partitions
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -506,7 +518,7 @@ __device__ inline Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const F
         if (W.deg[i] == 1) atomicOr(&W.bitmap[W.rank[i] >> 5], 1u << (W.rank[i] & 31));
     __syncthreads();
 
-    if (B.warp == 0) {
+    if (B.warp == B.sw) {
         const int lane = B.lane;
         for (int k = 0; k < p; ++k) {
             unsigned best = 0xffffffffu;
@@ -678,8 +690,8 @@ __device__ __forceinline__ void solve_row(WS<T>& W, int r, int g, int G, T* rvec
 
 // Runs rows level by level. Levels wider than two warps use every thread of
 // the CTA (one row per thread) and a CTA barrier; narrower levels (most of
-// them: the schedules are deep and thin) run on warp 0 with G lanes per row
-// and warp barriers.
+// them: the schedules are deep and thin) run on one warp (B.sw) with G lanes
+// per row and warp barriers.
 template <typename T, bool kBack, bool kScale = true>
 __device__ inline void level_sweep(Blk& B, WS<T>& W, const uint32_t* ptr, const uint16_t* rows,
                                    int nlev, T* rvec, T* out, T alpha) {
@@ -696,13 +708,68 @@ __device__ inline void level_sweep(Blk& B, WS<T>& W, const uint32_t* ptr, const 
             __syncthreads();
             warp_mode = false;
         } else {
-            if (B.warp == 0) {
+            if (B.warp == B.sw) {
                 const int G = cnt <= 4 ? 8 : cnt <= 8 ? 4 : cnt <= 16 ? 2 : 1;
                 const int per = 32 / G;
                 for (int base = i0; base < i1; base += per) {
                     int idx = base + B.lane / G;
                     solve_row<T, kBack, kScale>(W, idx < i1 ? rows[idx] : -1, B.lane & (G - 1), G,
                                                 rvec, out, alpha);
+                }
+                __syncwarp();
+            }
+            warp_mode = true;
+        }
+    }
+    if (warp_mode) __syncthreads();
+}
+
+// The same two sweeps in FP32 on the M-solve vectors rf -> zf (LPDEC_M32):
+// no fused PCG update, so the serial chain of each level holds only FP32
+// arithmetic (GB300's FP64 pipe retires a warp instruction every few dozen
+// cycles, FP32 every cycle).
+template <bool kBack, typename T>
+__device__ __forceinline__ void solve_row32(WS<T>& W, int r, int g, int G) {
+    float acc = 0.0f;
+    if (r >= 0) {
+        const uint32_t* ptr = kBack ? W.bptr : W.fptr;
+        const uint16_t* dep = kBack ? W.bdep : W.fdep;
+        const int k1 = ptr[r + 1];
+        for (int k = ptr[r] + g; k < k1; k += G) {
+            uint16_t ent = dep[k];
+            float v = W.zf[ent & kIdx];
+            acc += (ent & kNeg) ? -v : v;
+        }
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o, G);
+    if (r >= 0 && g == 0) {
+        float v = (kBack ? W.rf[r] : W.zf[r] * W.ip32[r]) - acc;
+        W.zf[r] = W.psgn[r] ? -v : v;
+    }
+}
+
+template <bool kBack, typename T>
+__device__ inline void level_sweep32(Blk& B, WS<T>& W, const uint32_t* ptr, const uint16_t* rows,
+                                     int nlev) {
+    bool warp_mode = false;
+    for (int lev = 1; lev <= nlev; ++lev) {
+        const int i0 = ptr[lev], i1 = ptr[lev + 1];
+        const int cnt = i1 - i0;
+        if (cnt > 64 && B.nt > 32) {
+            if (warp_mode) __syncthreads();
+            for (int base = i0; base < i1; base += B.nt) {
+                int idx = base + B.tid;
+                solve_row32<kBack>(W, idx < i1 ? rows[idx] : -1, 0, 1);
+            }
+            __syncthreads();
+            warp_mode = false;
+        } else {
+            if (B.warp == B.sw) {
+                const int G = cnt <= 4 ? 8 : cnt <= 8 ? 4 : cnt <= 16 ? 2 : 1;
+                const int per = 32 / G;
+                for (int base = i0; base < i1; base += per) {
+                    int idx = base + B.lane / G;
+                    solve_row32<kBack>(W, idx < i1 ? rows[idx] : -1, B.lane & (G - 1), G);
                 }
                 __syncwarp();
             }
@@ -726,6 +793,13 @@ __device__ inline void msolve(Blk& B, const CodeView& C, WS<T>& W, const Levels&
     level_sweep<T, false>(B, W, W.lfptr, W.lfrows, L.nf, rvec, out, alpha);
 }
 
+// M-solve in FP32: zf = M^-1 rf (rf written by the caller before a barrier).
+template <typename T>
+__device__ inline void msolve32(Blk& B, WS<T>& W, const Levels& L) {
+    level_sweep32<true>(B, W, W.lbptr, W.lbrows, L.nb);
+    level_sweep32<false>(B, W, W.lfptr, W.lfrows, L.nf);
+}
+
 // l = Q h = A D^2 A' h (matrix-free; t holds D^2 A' h over the standard
 // columns). Returns h'l in FP64.
 template <typename T>
@@ -747,8 +821,13 @@ __device__ inline double spmv_Q(Blk& B, const CodeView& C, WS<T>& W, const Frame
 // the residual), x0 = 0, stopping when ||r||_2 < tol ||rhs||_2 or after
 // max_it iterations. Dot products accumulate in FP64.
 template <typename T>
+__device__ inline int pcg_m32(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                              const Levels& L, double tol, int max_it, double* relres);
+
+template <typename T>
 __device__ inline int pcg(Blk& B, const CodeView& C, WS<T>& W, const Frame& F, const Levels& L,
-                          double tol, int max_it, double* relres) {
+                          double tol, int max_it, double* relres, bool m32 = false) {
+    if (m32) return pcg_m32<T>(B, C, W, F, L, tol, max_it, relres);
     const int p = F.p;
     for (int r = B.tid; r < p; r += B.nt) W.xs[r] = T(0);
     __syncthreads();
@@ -780,6 +859,69 @@ __device__ inline int pcg(Blk& B, const CodeView& C, WS<T>& W, const Frame& F, c
         zr = s.x;
         rr = s.y;
         for (int r = B.tid; r < p; r += B.nt) W.h[r] = W.z[r] + nu * W.h[r];
+        __syncthreads();
+        ++it;
+    }
+    *relres = isfinite(rr) ? sqrt(rr) / rn0 : INFINITY;
+    return it;
+}
+
+__device__ inline double3 bsum3(Blk& B, double a, double b, double c) {
+    double2 ab = bsum2(B, a, b);
+    return make_double3(ab.x, ab.y, bsum(B, c));
+}
+
+// PCG of LPDEC_M32: the Krylov recurrences, Q h and the dot products in
+// FP64 (type T = double), the preconditioner M^-1 (the two triangular
+// sweeps) in FP32. An FP32 M-solve is a slightly perturbed, not exactly
+// symmetric preconditioner, so the direction update uses the flexible
+// (Polak-Ribiere) coefficient nu = z_{k+1}'(r_{k+1} - r_k) / z_k'r_k
+// = -alpha z_{k+1}'l_k / z_k'r_k, which equals the Fletcher-Reeves value
+// of Algorithm 4 when M^-1 is applied exactly.
+template <typename T>
+__device__ inline int pcg_m32(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                              const Levels& L, double tol, int max_it, double* relres) {
+    const int p = F.p;
+    for (int r = B.tid; r < p; r += B.nt) { W.xs[r] = T(0); W.rf[r] = (float)W.r[r]; }
+    __syncthreads();
+    msolve32<T>(B, W, L);
+    double zr0 = 0.0, rr0 = 0.0;
+    for (int r = B.tid; r < p; r += B.nt) {
+        const double zv = (double)W.zf[r];
+        W.h[r] = (T)zv;
+        zr0 += zv * (double)W.r[r];
+        rr0 += (double)W.r[r] * (double)W.r[r];
+    }
+    double2 s = bsum2(B, zr0, rr0);
+    double zr = s.x, rr = s.y;
+    const double rn0 = sqrt(rr);
+    *relres = 0.0;
+    if (rn0 == 0.0) return 0;
+    int it = 0;
+    while (sqrt(rr) >= tol * rn0 && it < max_it) {
+        double hl = spmv_Q<T>(B, C, W, F, W.h, W.l);
+        if (!(hl > 0.0) || !isfinite(hl) || !(zr > 0.0)) break;
+        const double alpha = zr / hl;
+        for (int r = B.tid; r < p; r += B.nt) {
+            const double rv = (double)W.r[r] - alpha * (double)W.l[r];
+            W.r[r] = (T)rv;
+            W.xs[r] = (T)((double)W.xs[r] + alpha * (double)W.h[r]);
+            W.rf[r] = (float)rv;
+        }
+        __syncthreads();
+        msolve32<T>(B, W, L);
+        double zr_l = 0.0, rr_l = 0.0, zl_l = 0.0;
+        for (int r = B.tid; r < p; r += B.nt) {
+            const double zv = (double)W.zf[r];
+            zr_l += zv * (double)W.r[r];
+            rr_l += (double)W.r[r] * (double)W.r[r];
+            zl_l += zv * (double)W.l[r];
+        }
+        double3 s3 = bsum3(B, zr_l, rr_l, zl_l);
+        const double nu = -alpha * s3.z / zr;
+        zr = s3.x;
+        rr = s3.y;
+        for (int r = B.tid; r < p; r += B.nt) W.h[r] = (T)((double)W.zf[r] + nu * (double)W.h[r]);
         __syncthreads();
         ++it;
     }
@@ -822,12 +964,12 @@ __device__ inline void residual64(Blk& B, const CodeView& C, WS<T>& W, const Fra
 template <typename V, typename T>
 __device__ inline int refine_round(Blk& B, const CodeView& C, WS<V>& WV, WS<T>& W, const Frame& F,
                                    const Levels& L, double rn, double target, int budget,
-                                   double* rel) {
+                                   double* rel, bool m32 = false) {
     const int p = F.p;
     const double inv = 1.0 / rn;
     for (int r = B.tid; r < p; r += B.nt) WV.r[r] = (V)(W.r64[r] * inv);
     __syncthreads();
-    int it = pcg<V>(B, C, WV, F, L, target, budget, rel);
+    int it = pcg<V>(B, C, WV, F, L, target, budget, rel, m32);
     int bad = 0;
     for (int r = B.tid; r < p; r += B.nt) bad |= !isfinite((double)WV.xs[r]);
     bad = __syncthreads_or(bad);
@@ -866,7 +1008,8 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
             it = refine_round<T, T>(B, C, W, W, F, L, rn, target, min(fp32_cap, max_it - o.iters),
                                     &rel);
         } else if (sizeof(T) == 8) {
-            it = refine_round<T, T>(B, C, W, W, F, L, rn, target, max_it - o.iters, &rel);
+            it = refine_round<T, T>(B, C, W, W, F, L, rn, target, max_it - o.iters, &rel,
+                                    P.precision == LPDEC_M32);
             o.iters64 += it;
         } else {
             if (!view_ready) {
@@ -1215,6 +1358,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
         for (int r = B.tid; r < p; r += B.nt) {
             int pc = W.pivcol[r];
             W.invd2p[r] = pc < q ? (T)(1.0 / W.d2[pc]) : T(0);
+            if (P.precision == LPDEC_M32) W.ip32[r] = pc < q ? (float)(1.0 / W.d2[pc]) : 0.0f;
         }
         __syncthreads();
         const double tol = fmax(P.tol_pcg, fmin(1e-3, P.pcg_gap_factor * g_rel));

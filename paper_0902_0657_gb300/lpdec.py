@@ -29,6 +29,7 @@ LPDEC_MALP_A = 0
 LPDEC_MALP_B = 1
 LPDEC_FP64 = 0
 LPDEC_MIXED = 1
+LPDEC_M32 = 2
 
 
 class lpdec_params(ctypes.Structure):

@@ -48,7 +48,7 @@ def test_struct_sizes_match_header(lib):
 
 
 @pytest.mark.parametrize("name", ["gallager_120", "peg_1008", "gallager_504", "gallager_4032"])
-@pytest.mark.parametrize("precision", [L.LPDEC_FP64, L.LPDEC_MIXED])
+@pytest.mark.parametrize("precision", [L.LPDEC_FP64, L.LPDEC_MIXED, L.LPDEC_M32])
 @pytest.mark.parametrize("budget", [0, 4096, 20000, 60000, 100000])
 def test_workspace_layouts_validate(lib, name, precision, budget):
     c = named_code(name)
@@ -66,7 +66,7 @@ def test_workspace_ragged_sizes(lib):
         m = int(rng.integers(1, 400))
         n = int(rng.integers(1, 900))
         E = int(rng.integers(m, min(32 * m, 6 * n) + m + 1))
-        for prec in (0, 1):
+        for prec in (0, 1, 2):
             rc, smem, glob = L.lpdec_workspace_bytes(m, n, E, prec, int(rng.integers(0, 80000)))
             assert rc == 0
 
@@ -75,6 +75,11 @@ def test_workspace_rejects_bad_sizes(lib):
     for m, n, E in [(0, 10, 10), (10, 0, 10), (40000, 10, 10), (10, 40000, 10), (2, 10, 100)]:
         assert L.lpdec_workspace_bytes(m, n, E, 0, 0)[0] == L.LPDEC_ERR_INVALID_ARG
     assert L.lpdec_workspace_bytes(10, 20, 30, 7, 0)[0] == L.LPDEC_ERR_INVALID_ARG
+    # the FP32 M-solve vectors (3 x m floats) come on top of the FP64 layout
+    c = named_code("peg_1008")
+    s64 = L.lpdec_workspace_bytes(c.m, c.n, c.E, L.LPDEC_FP64, 0)[1]
+    s32 = L.lpdec_workspace_bytes(c.m, c.n, c.E, L.LPDEC_M32, 0)[1]
+    assert s32 - s64 == 12 * c.m
 
 
 def test_no_device_is_reported_not_emulated(lib):

@@ -30,11 +30,12 @@ def compare_frame(res, u, hard, cert, masks, st, ctx=""):
 
 
 @pytest.mark.parametrize("precision,threads", [(L.LPDEC_FP64, 128), (L.LPDEC_MIXED, 128),
-                                               (L.LPDEC_FP64, 32), (L.LPDEC_MIXED, 256)])
+                                               (L.LPDEC_M32, 128), (L.LPDEC_FP64, 32),
+                                               (L.LPDEC_MIXED, 256), (L.LPDEC_M32, 64)])
 def test_decode_gallager120_200_frames(precision, threads):
-    """(3,6) n=120, Eb/N0 2.0 dB, 200 frames from seed 0, in FP64 and in
-    mixed precision (FP32 PCG refined against FP64 residuals), at several
-    CTA sizes."""
+    """(3,6) n=120, Eb/N0 2.0 dB, 200 frames from seed 0, in FP64, in mixed
+    precision (FP32 PCG refined against FP64 residuals) and with the FP32
+    preconditioner solve, at several CTA sizes."""
     torch_cuda()
     code = named_code("gallager_120")
     G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(200))

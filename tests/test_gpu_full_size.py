@@ -1,0 +1,92 @@
+"""Parity at the benchmark's full size and launch configuration: the (3,6)
+PEG code n=1008, m=504 at Eb/N0 2.0 dB, one batch decoded by one persistent
+launch of the device entry point with the library's default parameters and
+layout, as bench.py times it.
+
+Every frame is checked for properties that hold at any size (Section II-B,
+Theorems 2-3, Corollary 5); sampled frames are compared with the oracle one
+by one (worker processes started with spawn), to the bar of the small-code
+parity tests: decisions, certificate, cut set and LP count bit-exact, u and
+the cost within 1e-6."""
+
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+from paper_0902_0657_gb300 import lpdec as L
+from synth import awgn_llr_frames, named_code
+
+from .gpu_util import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+NF = 456          # one frame per CTA of the default launch (3 per SM x 152)
+EBN0, SEED = 2.0, 0
+
+
+def _oracle_frame(f):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    import oracle
+    code = named_code("peg_1008")
+    g = awgn_llr_frames(code.n, code.design_rate, EBN0, SEED, [f])[0]
+    r = oracle.decode(code, g)
+    return f, r.status, r.hard, r.cert, r.masks, r.alp_iters, r.u, r.objective
+
+
+@pytest.fixture(scope="module")
+def batch():
+    torch_cuda()
+    code = named_code("peg_1008")
+    G = awgn_llr_frames(code.n, code.design_rate, EBN0, SEED, range(NF))
+    with L.Decoder(code) as d:
+        u, hard, cert, masks, st = d.decode_batch(G)
+    return code, G, u, hard, cert, masks, st
+
+
+def test_every_frame_properties(batch):
+    code, G, u, hard, cert, masks, st = batch
+    H = code.dense().astype(np.int64)
+    deg = np.diff(code.row_ptr)
+    ok = st["status"] == L.LPDEC_OK
+    assert set(np.unique(st["status"])) <= {L.LPDEC_OK, L.LPDEC_ERR_STALLED,
+                                            L.LPDEC_ERR_NOT_CONVERGED}
+    assert ok.mean() > 0.98
+    assert np.all(u >= -1e-9) and np.all(u <= 1 + 1e-9)                  # Theorem 2(a)
+    frac = np.abs(u - np.round(u)) > 1e-9
+    assert np.all(frac.sum(1) <= code.m)                                   # Corollary 5
+    assert np.array_equal(cert == 1, ~frac.any(1))
+    syn = (hard.astype(np.int64) @ H.T) % 2
+    assert not syn[cert == 1].any()                                        # Section II-B
+    assert np.allclose(st["objective"], (G * u).sum(1), rtol=1e-9, atol=1e-9)
+    for f in np.flatnonzero(ok)[:64]:
+        for j in np.flatnonzero(masks[f]):                                 # Theorem 3
+            mk = int(masks[f, j])
+            assert mk < (1 << deg[j]) and bin(mk).count("1") % 2 == 1
+            row = code.row(j)
+            sel = np.array([(mk >> k) & 1 for k in range(deg[j])], bool)
+            lhs = np.sum(1 - u[f, row[sel]]) + np.sum(u[f, row[~sel]])
+            assert lhs >= 1 - 1e-7, (f, j, lhs)                            # Eq. 6 holds
+
+
+def test_sampled_frames_match_oracle(batch):
+    code, G, u, hard, cert, masks, st = batch
+    ok = np.flatnonzero(st["status"] == L.LPDEC_OK)
+    sample = list(ok[:4]) + list(ok[cert[ok] == 0][:3])
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(len(sample), os.cpu_count() or 1)) as pool:
+        res = pool.map(_oracle_frame, [int(f) for f in sample])
+    n_frac = 0
+    for f, status, rh, rc, rm, ralp, ru, robj in res:
+        ctx_ = f"frame {f}"
+        assert st["status"][f] == status, ctx_
+        assert np.array_equal(hard[f], rh), ctx_
+        assert cert[f] == rc, ctx_
+        assert np.array_equal(masks[f], rm), ctx_
+        assert st["alp_iters"][f] == ralp, ctx_
+        assert np.max(np.abs(u[f] - ru)) <= 1e-6, ctx_
+        assert abs(st["objective"][f] - robj) <= 1e-6 * (1 + abs(robj)), ctx_
+        n_frac += rc == 0
+    assert n_frac >= 1
