@@ -54,9 +54,11 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=20000, help="frames per timed step per GPU")
-    ap.add_argument("--warmup-frames", type=int, default=152,
+    ap.add_argument("--warmup-frames", type=int, default=8,
                     help="frames per warm-up step (same kernel and code, fewer frames)")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "m32"], default="fp64",
+                    help="fp64: FP64 PCG; mixed: FP32 PCG refined in FP64; "
+                         "m32: FP64 PCG with an FP32 preconditioner solve")
     ap.add_argument("--threads", type=int, default=128)
     ap.add_argument("--smem-budget", type=int, default=0,
                     help="shared-memory bytes per CTA (0 = library choice)")
@@ -210,7 +212,7 @@ def run_ours(args):
     code = named_code(CODE_NAME)
     n, m, B_ = code.n, code.m, args.frames
     prm = L.lpdec_default_params()
-    prm.precision = L.LPDEC_MIXED if args.precision == "mixed" else L.LPDEC_FP64
+    prm.precision = {"fp64": L.LPDEC_FP64, "mixed": L.LPDEC_MIXED, "m32": L.LPDEC_M32}[args.precision]
     prm.threads_per_block = args.threads
     prm.smem_budget = args.smem_budget
     dec = L.Decoder(code, device=local, params=prm)
@@ -316,7 +318,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic", "config": workload_config(args, n, m),
         "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
         "roofline": roofline, "cpu_baseline": cpu,

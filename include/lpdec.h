@@ -95,10 +95,15 @@ extern "C" {
  *                     (an optimum that is not unique, where the adaptive loop
  *                     can cycle between two cut sets), keeping the last LP's
  *                     solution.
- *   max_alp = 200, max_ipm = 60, max_pcg = 2000 iteration caps (max_pcg per
+ *   max_alp = 200, max_ipm = 60, max_pcg = 1000 iteration caps (max_pcg per
  *                     Newton solve, over all refinement rounds; an LP whose
  *                     interior-point run converges needs at most ~40
- *                     iterations on the workloads measured)
+ *                     iterations on the workloads measured). A Newton solve
+ *                     whose PCG misses its tolerance within max_pcg (CG needs
+ *                     at most p steps in exact arithmetic, so it has stalled)
+ *                     is redone by a dense FP64 Cholesky factorization of
+ *                     A D^2 A' (LPs of up to 2048 rows), and so are the
+ *                     remaining Newton solves of that LP
  *   variant = LPDEC_MALP_A, precision = LPDEC_FP64
  * The decisions are taken on the LP's optimal vertex, recovered from the
  * final interior-point iterate through its strictly complementary
@@ -128,10 +133,13 @@ typedef struct lpdec_stats {
     int32_t vertex_failures;  /* LPs whose optimal-vertex recovery was rejected */
     int32_t max_levels;       /* deepest triangular-solve level schedule seen */
     int32_t pcg_iters_fp64;   /* PCG iterations run in FP64 (all of them in LPDEC_FP64) */
+    int32_t dense_solves;     /* Newton systems solved by the dense Cholesky fallback */
+    int32_t reserved;
     double  objective;        /* gamma'u */
-    double  pcg_flops;        /* algorithmic floating-point operations of the PCG
-                                 iterations (Q h, both triangular solves, dots,
-                                 updates) and the FP64 residuals of refinement */
+    double  pcg_flops;        /* algorithmic floating-point operations of the Newton
+                                 solves: PCG iterations (Q h, both triangular
+                                 solves, dots, updates), the FP64 residuals of
+                                 refinement and any dense fallback */
     double  seconds;          /* device time from the frame's start to its end
                                  (batch entry points: its time on its CTA) */
 } lpdec_stats;

@@ -166,7 +166,9 @@ k_pcg(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in
         for (int r = B.tid; r < F.p; r += B.nt) W.invd2p[r] = (T)(1.0 / W.d2[W.pivcol[r]]);
         __syncthreads();
         bool force64 = false;
-        NewtonOut no = newton_solve<T>(B, C, W, F, Lv, P, P.tol_pcg, P.max_pcg, force64);
+        bool force_dense = false;
+        NewtonOut no = newton_solve<T>(B, C, W, F, Lv, P, P.tol_pcg, P.max_pcg, force64,
+                                       force_dense);
         for (int r = B.tid; r < C.m; r += B.nt) dy[(size_t)f * C.m + r] = r < F.p ? W.dy[r] : 0.0;
         if (B.tid == 0) iters[f] = no.iters;
         __syncthreads();
@@ -307,7 +309,11 @@ bool layout_ok(const Layout& L, const std::vector<size_t>& sizes) {
 // budget; the bitmap and the level pointer arrays, which the kernels update
 // with shared-memory atomics, always do. The FP64 interior-point state goes
 // to per-CTA global scratch.
-Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes, bool m32) {
+// Largest LP (rows) for which the dense Cholesky fallback keeps its m x m
+// FP64 matrix in per-CTA scratch (32 MB at the limit).
+constexpr int kDenseMaxRows = 2048;
+
+Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes, bool m32, bool dense) {
     const size_t q = (size_t)n + m;
     size_t q2 = 1;
     while (q2 < q) q2 <<= 1;
@@ -334,6 +340,7 @@ Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes, bool m
         {G_VX, D * q, 2}, {G_V1, D * q, 2}, {G_V2, D * q, 2}, {G_V3, D * q, 2}, {G_V4, D * q, 2},
         {G_VR1, D * m, 2}, {G_VR2, D * m, 2},
         {G_P64, real_bytes < 8 ? D * vec_elems(n, m) : 16, 2},
+        {G_QD, dense ? D * (size_t)m * m : 16, 2},
     };
     Layout L{};
     size_t s = 0, g = 0;
@@ -351,6 +358,7 @@ Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes, bool m
     }
     L.smem_bytes = (uint32_t)s;
     L.q2 = (uint32_t)q2;
+    L.dense = dense ? 1u : 0u;
     L.gbytes = align_up(g, 256);
     if (specs.size() != (size_t)A_COUNT || !layout_ok(L, sizes)) L.smem_bytes = 0xffffffffu;
     return L;
@@ -378,7 +386,7 @@ int32_t plan(lpdec_ctx* ctx, const lpdec_code* code, int nframes, K kernel, size
     size_t budget = ctx->prm.smem_budget > 0 ? std::min((size_t)ctx->prm.smem_budget, cap)
                   : (third > per_cta ? std::min(cap, third - per_cta) : cap);
     Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes,
-                           ctx->prm.precision == LPDEC_M32);
+                           ctx->prm.precision == LPDEC_M32, code->m <= kDenseMaxRows);
     if (L.smem_bytes == 0xffffffffu) {
         snprintf(g_err, sizeof g_err, "inconsistent workspace layout");
         return LPDEC_ERR_INVALID_ARG;
@@ -395,7 +403,10 @@ int32_t plan(lpdec_ctx* ctx, const lpdec_code* code, int nframes, K kernel, size
         return LPDEC_ERR_INVALID_ARG;
     }
     int grid = std::max(1, std::min(nframes, per_sm * ctx->sm_count));
-    size_t need = (size_t)grid * L.gbytes;
+    // scratch for the full grid, whatever this batch needs, so that a small
+    // batch (a warm-up) leaves no allocation to a later, larger one
+    size_t need = (size_t)per_sm * ctx->sm_count * L.gbytes;
+    if (ctx->budget && need + ctx->staging_bytes > ctx->budget) need = (size_t)grid * L.gbytes;
     if (need > ctx->gscratch_bytes) {
         if (ctx->budget && need + ctx->staging_bytes > ctx->budget) return LPDEC_ERR_OUT_OF_BUDGET;
         if (ctx->gscratch) CK(cudaFree(ctx->gscratch));
@@ -474,7 +485,7 @@ void lpdec_default_params(lpdec_params* p) {
     p->tau_inc = 1e-9;
     p->max_alp = 200;
     p->max_ipm = 60;
-    p->max_pcg = 2000;
+    p->max_pcg = 1000;
     p->variant = LPDEC_MALP_A;
     p->precision = LPDEC_FP64;
 }
@@ -502,7 +513,7 @@ int32_t lpdec_workspace_bytes(int32_t m, int32_t n, int32_t E, int32_t precision
         return LPDEC_ERR_INVALID_ARG;
     size_t budget = smem_budget > 0 ? (size_t)smem_budget : (size_t)227 * 1024;
     Layout L = make_layout(n, m, E, budget, precision == LPDEC_MIXED ? 4 : 8,
-                           precision == LPDEC_M32);
+                           precision == LPDEC_M32, m <= kDenseMaxRows);
     if (L.smem_bytes == 0xffffffffu) return LPDEC_ERR_INVALID_ARG;
     if (smem_bytes) *smem_bytes = L.smem_bytes + sizeof(KernelShared);
     if (global_bytes_per_frame) *global_bytes_per_frame = (size_t)L.gbytes;
@@ -864,7 +875,7 @@ int32_t noalloc_launch_plan(const lpdec_params& prm, const lpdec_code* code, int
     size_t cap = (size_t)optin - sizeof(KernelShared) - 1024;
     size_t budget = prm.smem_budget > 0 ? std::min((size_t)prm.smem_budget, cap) : cap;
     Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes,
-                           prm.precision == LPDEC_M32);
+                           prm.precision == LPDEC_M32, false);
     if (L.smem_bytes == 0xffffffffu || L.smem_bytes + sizeof(KernelShared) > (size_t)optin) {
         snprintf(g_err, sizeof g_err, "frame workspace does not fit in shared memory");
         return LPDEC_ERR_INVALID_ARG;

@@ -63,6 +63,9 @@ enum Arr {
     // FP64 PCG vectors for the fallback rounds of the mixed mode (layout of
     // S_VEC with T = double)
     G_P64,
+    // dense p x p FP64 matrix of the Cholesky fallback of the Newton solve
+    // (16 bytes when the fallback is off)
+    G_QD,
     A_COUNT
 };
 
@@ -84,6 +87,7 @@ struct Layout {
     uint32_t off[A_COUNT];     // byte offset; kGlobalBit set = global scratch
     uint32_t smem_bytes;       // dynamic shared memory per CTA
     uint32_t q2;               // power of two >= n + m (sort width)
+    uint32_t dense;            // 1 = G_QD holds an m x m FP64 matrix
     unsigned long long gbytes; // global scratch bytes per CTA
 };
 
@@ -101,6 +105,7 @@ struct WS {
     unsigned long long* skey;   // aliases the PCG vectors
     double *x, *zz, *rc, *d2, *y, *b, *w, *dy, *r64, *u, *t64;
     double *vx, *v1, *v2, *v3, *v4, *vr1, *vr2, *p64;
+    double* qd;   // dense Cholesky factor (column-major p x p), null when off
 };
 
 __device__ __forceinline__ char* ws_ptr(const Layout& L, int a, char* smem, char* gws) {
@@ -139,6 +144,8 @@ __device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws, int n, i
     P_(double, vx, G_VX); P_(double, v1, G_V1); P_(double, v2, G_V2); P_(double, v3, G_V3);
     P_(double, v4, G_V4); P_(double, vr1, G_VR1); P_(double, vr2, G_VR2);
     P_(double, p64, G_P64);
+    P_(double, qd, G_QD);
+    if (!L.dense) w.qd = nullptr;
 #undef P_
     return w;
 }
@@ -165,7 +172,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W, int n, int m) {
     v.x = W.x; v.zz = W.zz; v.rc = W.rc; v.d2 = W.d2; v.y = W.y; v.b = W.b; v.w = W.w;
     v.dy = W.dy; v.r64 = W.r64; v.u = W.u; v.t64 = W.t64;
     v.vx = W.vx; v.v1 = W.v1; v.v2 = W.v2; v.v3 = W.v3; v.v4 = W.v4; v.vr1 = W.vr1;
-    v.vr2 = W.vr2; v.p64 = W.p64;
+    v.vr2 = W.vr2; v.p64 = W.p64; v.qd = W.qd;
     return v;
 }
 
@@ -937,7 +944,7 @@ __device__ inline int pcg_m32(Blk& B, const CodeView& C, WS<T>& W, const Frame& 
 // (FP32 cannot resolve the preconditioned system once D^2 spreads over many
 // decades near the optimum). Stops at ||r64|| < tol ||w||, when an FP64
 // round no longer halves ||r64||, or when the PCG budget is spent.
-struct NewtonOut { int iters, iters64; double relres, flops; };
+struct NewtonOut { int iters, iters64, dense; double relres, flops; };
 
 // Algorithmic floating-point operations of one PCG iteration (Algorithm 4):
 // Q h (2 passes over the pattern, D^2 and the slacks), the two triangular
@@ -945,6 +952,12 @@ struct NewtonOut { int iters, iters64; double relres, flops; };
 // products and the vector updates.
 __device__ __forceinline__ double pcg_iter_flops(const Frame& F, int n, int deps) {
     return 4.0 * F.ea + 2.0 * deps + n + 15.0 * F.p;
+}
+// ... and of one dense fallback solve: forming Q, the Cholesky
+// factorization (p^3 / 3), two triangular solves and the FP64 residual.
+__device__ __forceinline__ double dense_flops(const Frame& F, int n) {
+    const double p = F.p;
+    return p * p * p / 3.0 + 2.0 * p * p + 4.0 * F.ea + n + 3.0 * p;
 }
 
 template <typename V, typename T>
@@ -982,21 +995,104 @@ __device__ inline int refine_round(Blk& B, const CodeView& C, WS<V>& WV, WS<T>& 
     return it;
 }
 
+// Fallback Newton solve (A D^2 A') dy = w by a dense FP64 Cholesky
+// factorization Q = L L' (column-major, in W.qd), for the systems on which
+// PCG stalls (large degenerate LPs near the optimum, where the MTS
+// preconditioner of Section V no longer captures Q). This is the direct
+// method of the normal equations (Eq. 24); it leaves dy untouched and
+// returns false if the factorization meets a non-positive pivot.
+template <typename T>
+__device__ inline bool dense_newton(Blk& B, const CodeView& C, WS<T>& W, const Frame& F) {
+    const int n = C.n, p = F.p;
+    double* Lm = W.qd;
+    const size_t pp = (size_t)p * p;
+    for (size_t k = B.tid; k < pp; k += B.nt) Lm[k] = 0.0;
+    __syncthreads();
+    // Q(r, r2) = sum over the standard columns i of rows r, r2 of
+    // A(r,i) A(r2,i) d_i^2, plus d^2 of row r's slack on the diagonal; thread
+    // r writes only row r (entries (r2, r) of column r2), in a fixed order
+    for (int r = B.tid; r < p; r += B.nt) {
+        const int j = W.rowchk[r];
+        for (int e = C.h_ptr[j]; e < C.h_ptr[j + 1]; ++e) {
+            const uint16_t ent = W.rowent[e];
+            const int i = ent & kIdx;
+            const double dd = W.d2[i];
+            for (int k = C.v_ptr[i]; k < C.v_ptr[i + 1]; ++k) {
+                const uint16_t ce = W.colent[k];
+                if (ce == kNone) continue;
+                const int r2 = ce & kIdx;
+                Lm[(size_t)r2 * p + r] += ((ent ^ ce) & kNeg) ? -dd : dd;
+            }
+        }
+        Lm[(size_t)r * p + r] += W.d2[n + r];
+    }
+    __syncthreads();
+    // left-looking Cholesky, one column per step
+    for (int j = 0; j < p; ++j) {
+        double part = 0.0;
+        for (int k = B.tid; k < j; k += B.nt) {
+            const double v = Lm[(size_t)k * p + j];
+            part += v * v;
+        }
+        const double qjj = Lm[(size_t)j * p + j];
+        const double sjj = qjj - bsum(B, part);
+        if (!(sjj > 0.0) || !isfinite(sjj)) return false;   // same value in every thread
+        const double ljj = sqrt(sjj), inv = 1.0 / ljj;
+        for (int i = j + 1 + B.tid; i < p; i += B.nt) {
+            double acc = Lm[(size_t)j * p + i];
+            for (int k = 0; k < j; ++k) acc -= Lm[(size_t)k * p + i] * Lm[(size_t)k * p + j];
+            Lm[(size_t)j * p + i] = acc * inv;
+        }
+        if (B.tid == 0) Lm[(size_t)j * p + j] = ljj;
+        __syncthreads();
+    }
+    // L y = w (y into dy), then L' dy = y
+    for (int r = B.tid; r < p; r += B.nt) W.r64[r] = W.w[r];
+    __syncthreads();
+    for (int j = 0; j < p; ++j) {
+        const double yj = W.r64[j] / Lm[(size_t)j * p + j];
+        for (int i = j + 1 + B.tid; i < p; i += B.nt) W.r64[i] -= Lm[(size_t)j * p + i] * yj;
+        if (B.tid == 0) W.dy[j] = yj;
+        __syncthreads();
+    }
+    for (int j = p - 1; j >= 0; --j) {
+        double part = 0.0;
+        for (int i = j + 1 + B.tid; i < p; i += B.nt) part += Lm[(size_t)j * p + i] * W.dy[i];
+        const double yj = W.dy[j];
+        const double sum = bsum(B, part);
+        if (B.tid == 0) W.dy[j] = (yj - sum) / Lm[(size_t)j * p + j];
+        __syncthreads();
+    }
+    return true;
+}
+
 template <typename T>
 __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                          const Levels& L, const DevParams& P, double tol,
-                                         int max_it, bool& force64) {
+                                         int max_it, bool& force64, bool& force_dense) {
     const int p = F.p;
     double ww = 0.0;
     for (int r = B.tid; r < p; r += B.nt) { W.dy[r] = 0.0; W.r64[r] = W.w[r]; ww += W.w[r] * W.w[r]; }
     const double wn = sqrt(bsum(B, ww));
-    NewtonOut o{0, 0, 0.0, 0.0};
+    NewtonOut o{0, 0, 0, 0.0, 0.0};
     if (wn == 0.0) return o;
     const double it_flops = pcg_iter_flops(F, C.n, (int)(W.bptr[p] + W.fptr[p]));
     double rn = wn;
+    if (force_dense && dense_newton<T>(B, C, W, F)) {   // PCG already failed in this LP
+        double rr;
+        residual64<double, T>(B, C, W, F, &rr);
+        o.dense = 1;
+        o.relres = sqrt(rr) / wn;
+        o.flops += dense_flops(F, C.n);
+        return o;
+    }
     bool use64 = sizeof(T) == 8 || force64;
+    // LPDEC_M32: FP32 M-solves until one round stalls, then FP64 M-solves
+    // for the rest of this LP (force64 is sticky across its Newton solves)
+    bool m32 = P.precision == LPDEC_M32 && !force64;
     bool view_ready = false;
     const int fp32_cap = max(64, max_it / 8);   // one FP32 round; failing it switches to FP64
+    const int m32_cap = max(256, max_it / 4);   // one round with an FP32 M-solve
     WS<double> W64;
     for (int round = 0; round < 12; ++round) {
         if (rn < tol * wn || o.iters >= max_it) break;
@@ -1008,9 +1104,10 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
             it = refine_round<T, T>(B, C, W, W, F, L, rn, target, min(fp32_cap, max_it - o.iters),
                                     &rel);
         } else if (sizeof(T) == 8) {
-            it = refine_round<T, T>(B, C, W, W, F, L, rn, target, max_it - o.iters, &rel,
-                                    P.precision == LPDEC_M32);
-            o.iters64 += it;
+            it = refine_round<T, T>(B, C, W, W, F, L, rn, target,
+                                    m32 ? min(m32_cap, max_it - o.iters) : max_it - o.iters,
+                                    &rel, m32);
+            if (!m32) o.iters64 += it;
         } else {
             if (!view_ready) {
                 W64 = fp64_view<T>(W, C.n, C.m);
@@ -1031,11 +1128,23 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
         rn = rn_new;
         if (!use64) {
             if (!halved || missed) use64 = force64 = true;   // FP64 from here on in this LP
+        } else if (m32) {
+            if (!halved || missed) { m32 = false; force64 = true; }
         } else if (!halved) {
             break;
         }
     }
     o.relres = rn / wn;
+    if (o.relres > tol && W.qd != nullptr) {   // PCG stalled: direct solve, for the rest of the LP
+        force_dense = true;
+        if (dense_newton<T>(B, C, W, F)) {
+            double rr;
+            residual64<double, T>(B, C, W, F, &rr);
+            o.dense = 1;
+            o.relres = sqrt(rr) / wn;
+            o.flops += dense_flops(F, C.n);
+        }
+    }
     return o;
 }
 
@@ -1257,7 +1366,10 @@ __device__ inline int certify_basis(Blk& B, const CodeView& C, WS<T>& W, const F
 // ---------------------------------------------------------------------------
 // a3 + a6: infeasible primal-dual path-following method (Section IV-B)
 // ---------------------------------------------------------------------------
-struct IpmOut { int iters, pcg_iters, pcg_iters64, converged, certified, max_levels; double flops; };
+struct IpmOut {
+    int iters, pcg_iters, pcg_iters64, converged, certified, max_levels, dense;
+    double flops;
+};
 
 // trace (optional): per iteration 8 doubles {gap, feas_p, feas_d, PCG
 // iterations, Newton relative residual, beta_P, beta_D, levels}
@@ -1266,7 +1378,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
                                    const DevParams& P, const double* gamma, int q2,
                                    double* trace = nullptr, int max_trace = 0) {
     const int n = C.n, p = F.p, q = F.q;
-    IpmOut o{0, 0, 0, 0, 0, 0, 0.0};
+    IpmOut o{0, 0, 0, 0, 0, 0, 0, 0.0};
     // cold start x = e, y = 0, z = c + e
     double nc2 = 0.0;
     for (int i = B.tid; i < q; i += B.nt) {
@@ -1277,7 +1389,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
     }
     for (int r = B.tid; r < p; r += B.nt) W.y[r] = 0.0;
     F.normc = sqrt(bsum(B, nc2));   // (barrier inside)
-    bool force64 = false;
+    bool force64 = false, force_dense = false;
     int last_pcg = 0;
     double prev_grel = INFINITY, sig0 = -1.0, sig1 = -1.0;
     for (int it = 0;; ++it) {
@@ -1362,11 +1474,12 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
         }
         __syncthreads();
         const double tol = fmax(P.tol_pcg, fmin(1e-3, P.pcg_gap_factor * g_rel));
-        NewtonOut no = newton_solve<T>(B, C, W, F, L, P, tol, P.max_pcg, force64);
+        NewtonOut no = newton_solve<T>(B, C, W, F, L, P, tol, P.max_pcg, force64, force_dense);
+        o.dense += no.dense;
         o.pcg_iters += no.iters;
         o.pcg_iters64 += no.iters64;
         o.flops += no.flops;
-        last_pcg = no.iters;
+        last_pcg = no.dense ? 1000000 : no.iters;
         if (no.relres > 1e-3 && g_rel < 1e-6) {   // no usable direction left near the optimum
             o.iters = it;
             break;
@@ -1581,6 +1694,7 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
         st.ipm_iters_total += io.iters;
         st.pcg_iters_total += io.pcg_iters;
         st.pcg_iters_fp64 += io.pcg_iters64;
+        st.dense_solves += io.dense;
         st.pcg_flops += io.flops;
         st.max_levels = max(st.max_levels, io.max_levels);
         int ok = io.certified || certify<T>(B, C, W, F, gamma);

@@ -44,14 +44,15 @@ class lpdec_params(ctypes.Structure):
 class lpdec_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in
                 ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total", "lp_rows_final",
-                 "vertex_failures", "max_levels", "pcg_iters_fp64")] + \
+                 "vertex_failures", "max_levels", "pcg_iters_fp64", "dense_solves", "reserved")] + \
                [("objective", ctypes.c_double), ("pcg_flops", ctypes.c_double),
                 ("seconds", ctypes.c_double)]
 
 
 STATS_DTYPE = np.dtype([(k, np.int32) for k in
                         ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total",
-                         "lp_rows_final", "vertex_failures", "max_levels", "pcg_iters_fp64")] +
+                         "lp_rows_final", "vertex_failures", "max_levels", "pcg_iters_fp64",
+                         "dense_solves", "reserved")] +
                        [("objective", np.float64), ("pcg_flops", np.float64),
                         ("seconds", np.float64)])
 assert STATS_DTYPE.itemsize == ctypes.sizeof(lpdec_stats)

@@ -40,11 +40,11 @@ def test_all_declared_symbols_exported(lib):
 
 def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(L.lpdec_params) == 13 * 8 + 8 * 4
-    assert ctypes.sizeof(L.lpdec_stats) == 8 * 4 + 3 * 8
+    assert ctypes.sizeof(L.lpdec_stats) == 10 * 4 + 3 * 8
     p = L.lpdec_default_params()
     assert (p.sigma, p.eta, p.tol_gap, p.tol_feas) == (0.1, 0.99, 1e-8, 1e-8)
     assert (p.tau_act, p.tau_cut, p.tau_int, p.tau_inc) == (1e-9, 1e-9, 1e-9, 1e-9)
-    assert (p.max_alp, p.max_ipm, p.max_pcg, p.variant, p.precision) == (200, 60, 2000, 0, 0)
+    assert (p.max_alp, p.max_ipm, p.max_pcg, p.variant, p.precision) == (200, 60, 1000, 0, 0)
 
 
 @pytest.mark.parametrize("name", ["gallager_120", "peg_1008", "gallager_504", "gallager_4032"])
