@@ -1000,7 +1000,10 @@ __device__ inline int refine_round(Blk& B, const CodeView& C, WS<V>& WV, WS<T>& 
 // PCG stalls (large degenerate LPs near the optimum, where the MTS
 // preconditioner of Section V no longer captures Q). This is the direct
 // method of the normal equations (Eq. 24); it leaves dy untouched and
-// returns false if the factorization meets a non-positive pivot.
+// returns false if Q has a non-finite entry or a non-positive diagonal.
+constexpr double kPivotTiny = 1e-13;
+constexpr double kPivotHuge = 1e64;
+
 template <typename T>
 __device__ inline bool dense_newton(Blk& B, const CodeView& C, WS<T>& W, const Frame& F) {
     const int n = C.n, p = F.p;
@@ -1036,8 +1039,14 @@ __device__ inline bool dense_newton(Blk& B, const CodeView& C, WS<T>& W, const F
         }
         const double qjj = Lm[(size_t)j * p + j];
         const double sjj = qjj - bsum(B, part);
-        if (!(sjj > 0.0) || !isfinite(sjj)) return false;   // same value in every thread
-        const double ljj = sqrt(sjj), inv = 1.0 / ljj;
+        if (!isfinite(sjj) || !(qjj > 0.0)) return false;   // same values in every thread
+        // A pivot at the rounding level of Q(j,j) means Q is singular to
+        // working precision along y_j (a degenerate optimum): it is given a
+        // huge value, which zeroes that component of the step instead of
+        // amplifying rounding noise (the usual treatment of tiny pivots in
+        // interior-point normal equations).
+        const bool tiny = !(sjj > kPivotTiny * qjj);
+        const double ljj = tiny ? kPivotHuge : sqrt(sjj), inv = 1.0 / ljj;
         for (int i = j + 1 + B.tid; i < p; i += B.nt) {
             double acc = Lm[(size_t)j * p + i];
             for (int k = 0; k < j; ++k) acc -= Lm[(size_t)k * p + i] * Lm[(size_t)k * p + j];
