@@ -292,6 +292,47 @@ int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
                                           uint32_t* d_cut_mask, lpdec_stats* d_stats,
                                           void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: frames submitted one at a time as they arrive, decoded in batches
+ * that overlap on the GPU. The paper has no counterpart (it decodes one frame
+ * at a time); each frame is still decoded by Algorithm 3 exactly as by
+ * lpdec_decode, and its result does not depend on the frames it is batched
+ * with.
+ *
+ * A server owns `lanes` decoder contexts on `device` (each with its own
+ * stream, scratch and copy of the code H given in CSR as for
+ * lpdec_code_create), each with buffers for `batch` frames. A worker thread
+ * starts a batch of queued frames on every idle lane; while one lane's batch
+ * finishes its slowest frames, the next lane's batch takes the SMs it frees.
+ * `params` as for lpdec_ctx_create (NULL = defaults). At most `max_pending`
+ * submitted frames may be outstanding (queued, running, or finished and not
+ * yet polled). Device memory: about lanes x (scratch of a full grid + 2 x
+ * batch x (9n + 64) bytes). Returns LPDEC_ERR_NO_DEVICE without a usable
+ * GPU, LPDEC_ERR_INVALID_ARG for bad arguments (lanes 1..16, batch >= 1,
+ * max_pending >= 1, a CSR as for lpdec_code_create). */
+typedef struct lpdec_server lpdec_server;
+int32_t lpdec_server_create(int32_t device, const lpdec_params* params, int32_t m, int32_t n,
+                            const int32_t* row_ptr, const int32_t* col_idx, int32_t lanes,
+                            int32_t batch, int32_t max_pending, lpdec_server** out);
+
+/* Queues one frame: gamma = n host FP64 LLRs (copied before return). Writes
+ * the frame's ticket (0, 1, 2, ... in submission order). Returns
+ * LPDEC_ERR_OUT_OF_BUDGET when max_pending frames are outstanding,
+ * LPDEC_ERR_INVALID_ARG for a non-finite LLR, or the server's sticky error
+ * after a failed CUDA call. */
+int32_t lpdec_submit(lpdec_server* server, const double* gamma, uint64_t* ticket);
+
+/* Result of one ticket, once: u (n FP64), hard (n bytes), cert and stats
+ * (any output may be NULL), then the ticket is released. Returns
+ * LPDEC_ERR_PENDING while the frame is queued or running,
+ * LPDEC_ERR_INVALID_ARG for a ticket never issued or already polled, or the
+ * server's sticky error. Never blocks on the GPU. */
+int32_t lpdec_poll(lpdec_server* server, uint64_t ticket, double* u_out, uint8_t* hard_out,
+                   int32_t* cert_out, lpdec_stats* stats);
+
+/* Drops the queued frames, waits for the running batches, frees everything. */
+int32_t lpdec_server_destroy(lpdec_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,8 +40,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + ".tmp"
+    units = [os.path.join(SRC, f) for f in ("lpdec.cu", "serve.cu")]
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
-           "-Xcompiler", "-fPIC", "-o", tmp, os.path.join(SRC, "lpdec.cu")]
+           "-Xcompiler", "-fPIC", "-o", tmp, *units]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -103,6 +103,13 @@ def _load():
     lib.lpdec_lp_solve_trace_device.argtypes = [P, P, i32, P, P, P, P, P, P, i32, P]
     lib.lpdec_decode_batch_device_noalloc.argtypes = [P, ctypes.POINTER(lpdec_params), i32, P, P,
                                                       P, P, P, P, P]
+    lib.lpdec_server_create.argtypes = [i32, ctypes.POINTER(lpdec_params), i32, i32, P, P, i32,
+                                        i32, i32, ctypes.POINTER(P)]
+    lib.lpdec_submit.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.lpdec_poll.argtypes = [P, ctypes.c_uint64, P, P, P, P]
+    lib.lpdec_server_destroy.argtypes = [P]
+    for name in ("lpdec_server_create", "lpdec_submit", "lpdec_poll", "lpdec_server_destroy"):
+        getattr(lib, name).restype = i32
     for name in ("lpdec_ctx_create", "lpdec_ctx_set_params", "lpdec_code_create",
                  "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_batch_device",
                  "lpdec_cut_search_device", "lpdec_mts_select_device", "lpdec_pcg_device",
@@ -316,6 +323,78 @@ class Decoder:
         if self.ctx:
             lpdec_ctx_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ---------------------------------------------------------------------------
+# Serving (lpdec_server_create / lpdec_submit / lpdec_poll)
+# ---------------------------------------------------------------------------
+
+def lpdec_server_create(device: int, params: lpdec_params | None, code, lanes: int = 2,
+                        batch: int = 512, max_pending: int = 1 << 16):
+    rp = np.ascontiguousarray(code.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(code.col_idx, dtype=np.int32)
+    out = ctypes.c_void_p()
+    rc = _load().lpdec_server_create(device, ctypes.byref(params) if params is not None else None,
+                                     code.m, code.n, rp.ctypes.data, ci.ctypes.data, lanes,
+                                     batch, max_pending, ctypes.byref(out))
+    _check(rc, "lpdec_server_create")
+    return out.value
+
+
+def lpdec_submit(server, gamma) -> tuple[int, int]:
+    """Returns (status, ticket)."""
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    t = ctypes.c_uint64()
+    rc = _load().lpdec_submit(server, g.ctypes.data, ctypes.byref(t))
+    return rc, t.value
+
+
+def lpdec_poll(server, ticket: int, u_out=None, hard_out=None, cert_out=None, stats_out=None):
+    return _load().lpdec_poll(server, ticket, _hptr(u_out, np.float64),
+                              _hptr(hard_out, np.uint8), _hptr(cert_out, np.int32),
+                              None if stats_out is None else stats_out.ctypes.data)
+
+
+def lpdec_server_destroy(server):
+    return _load().lpdec_server_destroy(server)
+
+
+class Server:
+    """Submit frames as they arrive, poll their results (a thin wrapper of
+    the C serving entry points)."""
+
+    def __init__(self, code, device: int = 0, params: lpdec_params | None = None,
+                 lanes: int = 2, batch: int = 512, max_pending: int = 1 << 16):
+        self.n = code.n
+        self.handle = lpdec_server_create(device, params, code, lanes, batch, max_pending)
+
+    def submit(self, gamma) -> int:
+        rc, t = lpdec_submit(self.handle, gamma)
+        _check(rc, "lpdec_submit")
+        return t
+
+    def poll(self, ticket: int):
+        """(u, hard, cert, stats) once the frame is decoded, else None."""
+        u = np.empty(self.n, np.float64)
+        h = np.empty(self.n, np.uint8)
+        c = np.zeros(1, np.int32)
+        st = np.zeros(1, STATS_DTYPE)
+        rc = lpdec_poll(self.handle, ticket, u, h, c, st)
+        if rc == LPDEC_ERR_PENDING:
+            return None
+        _check(rc, "lpdec_poll")
+        return u, h, int(c[0]), st[0]
+
+    def close(self):
+        if self.handle:
+            lpdec_server_destroy(self.handle)
+            self.handle = None
 
     def __enter__(self):
         return self

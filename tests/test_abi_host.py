@@ -97,3 +97,24 @@ def test_null_handles_rejected(lib):
     assert rc == L.LPDEC_ERR_INVALID_ARG
     rc = lib.lpdec_ctx_set_params(None, None)
     assert rc == L.LPDEC_ERR_INVALID_ARG
+
+
+def test_server_reports_missing_device_and_null_handles(lib):
+    import torch
+    code = named_code("gallager_120")
+    if not torch.cuda.is_available():
+        with pytest.raises(L.LpdecError) as e:
+            L.Server(code)
+        assert e.value.code == L.LPDEC_ERR_NO_DEVICE
+    assert lib.lpdec_submit(None, None, None) == L.LPDEC_ERR_INVALID_ARG
+    assert lib.lpdec_poll(None, 0, None, None, None, None) == L.LPDEC_ERR_INVALID_ARG
+    assert lib.lpdec_server_destroy(None) == L.LPDEC_ERR_INVALID_ARG
+    bad = L.lpdec_params()
+    L.library().lpdec_default_params(ctypes.byref(bad))
+    out = ctypes.c_void_p()
+    rp = np.array([0, 2], np.int32)
+    ci = np.array([0, 1], np.int32)
+    for lanes, batch, pend in ((0, 4, 4), (17, 4, 4), (1, 0, 4), (1, 4, 0)):
+        rc = lib.lpdec_server_create(0, ctypes.byref(bad), 1, 2, rp.ctypes.data, ci.ctypes.data,
+                                     lanes, batch, pend, ctypes.byref(out))
+        assert rc == L.LPDEC_ERR_INVALID_ARG

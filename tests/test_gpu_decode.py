@@ -158,3 +158,19 @@ def test_stall_rule_matches_oracle():
         res = oracle.decode(code, G[f], OracleParams(tau_inc=1e6))
         compare_frame(res, u[f], hard[f], cert[f], masks[f], st[f], f"frame {f}")
         assert res.alp_iters == 0 or (res.status == L.LPDEC_ERR_STALLED and res.alp_iters == 1)
+
+
+def test_malp_b_matches_oracle():
+    """MALP-B (Section III-A: every inactive inequality is dropped before the
+    search) against the oracle's MALP-B on the n=120 workload."""
+    from oracle.params import OracleParams
+    torch_cuda()
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(100))
+    prm = L.lpdec_default_params()
+    prm.variant = L.LPDEC_MALP_B
+    with L.Decoder(code, params=prm) as d:
+        u, hard, cert, masks, st = d.decode_batch(G)
+    for f in range(100):
+        res = oracle.decode(code, G[f], OracleParams(variant="malp_b"))
+        compare_frame(res, u[f], hard[f], cert[f], masks[f], st[f], f"frame {f}")
