@@ -66,7 +66,8 @@ class DecodeResult:
     masks: np.ndarray          # uint32 [m] (0 where not in the LP)
     alp_iters: int             # number of LPs solved
     ipm_iters_total: int
-    lp_rows_final: int
+    lp_rows_final: int         # rows of the last LP solved (MALP-B drops
+                               # inactive inequalities after it, Section III-A)
     objective: float           # gamma'u
     status: int
     history: list              # LPRecord per LP solved
@@ -168,7 +169,7 @@ def decode(code, gamma, params: OracleParams | None = None,
     return DecodeResult(u=u, hard=hard, cert=cert, in_lp=in_lp.copy(),
                         masks=out_masks, alp_iters=lps,
                         ipm_iters_total=ipm_total,
-                        lp_rows_final=len(final_cuts),
+                        lp_rows_final=history[-1].p if history else 0,
                         objective=float(np.dot(gamma, u)), status=status,
                         history=history, cuts=final_cuts,
                         vertex_failures=vfail)
