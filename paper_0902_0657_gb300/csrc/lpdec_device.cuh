@@ -855,7 +855,14 @@ __device__ inline int pcg(Blk& B, const CodeView& C, WS<T>& W, const Frame& F, c
         double hl = spmv_Q<T>(B, C, W, F, W.h, W.l);
         if (!(hl > 0.0) || !isfinite(hl)) break;   // lost positive curvature (rounding)
         T alpha = (T)(zr / hl);
-        msolve<T>(B, C, W, L, W.r, W.z, alpha);   // fused r -= a l, xs += a h
+        // r -= a l, xs += a h over all warps, then the M-solve: the serial
+        // sweeps keep only the substitution itself
+        for (int r = B.tid; r < p; r += B.nt) {
+            W.r[r] -= alpha * W.l[r];
+            W.xs[r] += alpha * W.h[r];
+        }
+        __syncthreads();
+        msolve<T>(B, C, W, L, W.r, W.z, T(0));
         double zr_l = 0.0, rr_l = 0.0;
         for (int r = B.tid; r < p; r += B.nt) {
             zr_l += (double)W.z[r] * (double)W.r[r];
