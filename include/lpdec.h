@@ -156,9 +156,12 @@ const char* lpdec_error_string(int32_t code);
 /* Host-only (no device needed): the per-frame workspace of a code with m
  * checks, n bits and E edges in the given precision mode — shared memory
  * per CTA (*smem_bytes) and global scratch per concurrently decoded frame
- * (*global_bytes_per_frame) — for a shared-memory budget per CTA
- * (smem_budget <= 0: the default). Also validates the layout (every array
- * aligned, inside its region, disjoint from the others). */
+ * (*global_bytes_per_frame, including the dense fallback's m x m FP64
+ * matrix when m <= 2048) — for a shared-memory budget per CTA
+ * (smem_budget <= 0: 227 KB, the largest layout; the decoder itself
+ * defaults to a third of the SM's shared memory, 75 KB on GB300). Also
+ * validates the layout (every array aligned, inside its region, disjoint
+ * from the others). */
 int32_t lpdec_workspace_bytes(int32_t m, int32_t n, int32_t E, int32_t precision,
                               int32_t smem_budget, size_t* smem_bytes,
                               size_t* global_bytes_per_frame);

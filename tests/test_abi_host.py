@@ -47,7 +47,8 @@ def test_struct_sizes_match_header(lib):
     assert (p.max_alp, p.max_ipm, p.max_pcg, p.variant, p.precision) == (200, 60, 1000, 0, 0)
 
 
-@pytest.mark.parametrize("name", ["gallager_120", "peg_1008", "gallager_504", "gallager_4032"])
+@pytest.mark.parametrize("name", ["gallager_120", "peg_1008", "gallager_504", "gallager_4032",
+                                  "gallager_16000", "gallager330_8000"])
 @pytest.mark.parametrize("precision", [L.LPDEC_FP64, L.LPDEC_MIXED, L.LPDEC_M32])
 @pytest.mark.parametrize("budget", [0, 4096, 20000, 60000, 100000])
 def test_workspace_layouts_validate(lib, name, precision, budget):

@@ -131,3 +131,45 @@ def test_pcg_newton_solver_reproduces_cholesky_ipm():
                        solve_normal=mts.pcg_normal_solver(L.A, code.n, "colwise", 1e-10, 2000))
         assert r2.status == 0
         assert np.max(np.abs(L.u_from_x(r1.x) - L.u_from_x(r2.x))) < 1e-6
+
+
+def _kappas(A, d2):
+    """cond(Q) and cond(M^-1 Q) for Q = A D^2 A' and the column-wise MTS
+    M = A_M D_M^2 A_M', from singular values of D-scaled factors (no
+    product is formed: cond(Q) = cond(A D)^2, and M^-1 Q is similar to
+    B B' with B = D_M^-1 A_M^-1 A D)."""
+    d = np.sqrt(d2)
+    AD = A * d
+    s = np.linalg.svd(AD, compute_uv=False)
+    col, row = mts.colwise(A, d2)
+    B = np.linalg.solve(A[:, col], AD) / d[col][:, None]
+    s2 = np.linalg.svd(B, compute_uv=False)
+    return (s[0] / s[-1]) ** 2, (s2[0] / s2[-1]) ** 2, col, row
+
+
+def test_mts_clusters_the_spectrum_near_an_integral_optimum():
+    """Section VI: as the interior-point method approaches an integral
+    optimum, Q = A D^2 A' becomes very ill-conditioned while the MTS
+    preconditioner keeps M^-1 Q well conditioned, so PCG needs few
+    iterations where plain CG would need many (Figs. 5-6)."""
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(12))
+    prm = OracleParams()
+    checked = 0
+    for g in G:
+        res = oracle.decode(code, g)
+        if res.cert != 1 or not res.history:
+            continue
+        h = res.history[-1]
+        L = lp.build(code, g, h.in_lp, h.masks)
+        tr = []
+        ipm.solve(L.A, L.b, L.c, prm, trace=tr)
+        kq, kp, col, row = _kappas(L.A, tr[-1]["d2"])
+        assert kq > 1e12 and kp < 1e3, (kq, kp)
+        p = L.A.shape[0]
+        w = np.random.default_rng(0).normal(size=p)
+        rs = []
+        mts.pcg(L.A, tr[-1]["d2"], w, col, row, 1e-8, 5 * p, residuals=rs)
+        assert len(rs) - 1 <= p, len(rs)
+        checked += 1
+    assert checked >= 5
