@@ -173,3 +173,67 @@ def test_mts_clusters_the_spectrum_near_an_integral_optimum():
         assert len(rs) - 1 <= p, len(rs)
         checked += 1
     assert checked >= 5
+
+
+def _cg_iters(Q, w, tol, max_it):
+    """Plain CG (no preconditioner) iterations to ||r|| < tol ||w||."""
+    x = np.zeros_like(w)
+    r = w.copy()
+    h = r.copy()
+    wn = np.linalg.norm(w)
+    it = 0
+    while np.linalg.norm(r) >= tol * wn and it < max_it:
+        l = Q @ h
+        a = (r @ r) / (h @ l)
+        x += a * h
+        rn = r - a * l
+        h = rn + (rn @ rn) / (r @ r) * h
+        r = rn
+        it += 1
+    return it
+
+
+def test_preconditioners_against_plain_cg():
+    """Section VI-B (Figs. 5-8): on the last LP of MALP-A decodings of a
+    (3,6) n=480 code at 1.5 dB, plain CG stops converging as the interior
+    point nears the optimum, while PCG with each MTS preconditioner
+    (Algorithms 6, 7, 8) converges in far fewer iterations; in the
+    ill-conditioned late iterations of fractional LPs the incremental search
+    is the most effective and does at least as well as the row-wise one."""
+    code = named_code("gallager_480")
+    G = awgn_llr_frames(code.n, code.design_rate, 1.5, 0, range(4))
+    prm = OracleParams()
+    cap = 1000
+    inc_late = row_late = 0
+    n_int = 0
+    for g in G:
+        res = oracle.decode(code, g)
+        h = res.history[-1]
+        L = lp.build(code, g, h.in_lp, h.masks)
+        tr = []
+        ipm.solve(L.A, L.b, L.c, prm, trace=tr)
+        p = L.A.shape[0]
+        w = np.random.default_rng(0).normal(size=p)
+        for t in (tr[(2 * len(tr)) // 3], tr[-1]):
+            d2 = t["d2"]
+            Q = (L.A * d2) @ L.A.T
+            cg = _cg_iters(Q, w, 1e-4, cap)
+            its = {}
+            for name, (col, row) in (("col", mts.colwise(L.A, d2)),
+                                     ("inc", mts.incremental(L.A, d2)),
+                                     ("row", mts.rowwise(L.A, d2, code.n))):
+                rs = []
+                mts.pcg(L.A, d2, w, col, row, 1e-4, cap, residuals=rs)
+                its[name] = len(rs) - 1
+            if t is tr[-1]:
+                assert min(its.values()) < cg, (its, cg)   # CG at the cap
+            else:
+                assert min(its.values()) * 3 <= cg, (its, cg)
+            if res.cert == 1 and t is tr[-1]:
+                n_int += 1
+                assert cg == cap and max(its.values()) <= 60, (its, cg)
+            if res.cert == 0 and t is tr[-1]:
+                inc_late += its["inc"]
+                row_late += its["row"]
+                assert its["inc"] <= min(its["col"], its["row"]), its
+    assert n_int >= 1 and inc_late <= row_late
