@@ -335,6 +335,11 @@ def run_ours(args):
             "mean_ipm_iters_per_frame": float(st["ipm_iters_total"].mean()),
             "mean_pcg_iters_per_frame": float(st["pcg_iters_total"].mean()),
             "pcg_flops_per_step": flops / args.steps,
+            "pcg_spmv_hbm_gbs": None,
+            "pcg_spmv_hbm_note": ("Q h reads the frame's LP pattern and vectors from shared memory "
+                                  "and L2-resident per-CTA scratch; DRAM traffic of a whole decode "
+                                  "is ~31 KB per frame (ncu, small case), so the SpMV has no HBM "
+                                  "rate to report; the kernel's bound is reported in roofline"),
             "wall_s": wall,
         },
     }
