@@ -190,3 +190,28 @@ def test_stall_rule_follows_theorem_2b():
     r = oracle.decode(code, needs_lp[0], OracleParams(tau_inc=1e6))
     assert r.status == STALLED and r.alp_iters == 1
     assert np.array_equal(r.u, r.history[0].u)
+
+
+def test_theorem_2d_each_lp_solves_lp_decoding_of_its_active_checks():
+    """Theorem 2(d): the solution u^k of every intermediate LP is the LP
+    decoding solution (Eq. 7, all parity inequalities) of the Tanner graph
+    made of the check nodes whose inequalities are active at u^k."""
+    from synth.codes import from_rows
+    prm = OracleParams()
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 1.5, 21, range(5))
+    checked = 0
+    for g in G:
+        res = oracle.decode(code, g, prm)
+        for h in res.history:
+            J = h.rows[h.slack <= prm.tau_act]
+            sub = from_rows([list(code.row(j)) for j in J], code.n)
+            if len(J):
+                u_ref, f_ref = feldman.lp_decode(sub, g)
+            else:
+                u_ref = (g < 0).astype(float)
+                f_ref = float(g @ u_ref)
+            assert abs(h.objective - f_ref) <= 1e-9 * (1 + abs(f_ref))
+            assert np.max(np.abs(h.u - u_ref)) < 1e-7
+            checked += 1
+    assert checked >= 20
