@@ -218,8 +218,8 @@ int32_t lpdec_decode_batch_device(lpdec_ctx* ctx, const lpdec_code* code,
  * slacks (Eq. 16). Per-frame vectors over columns use a stride of n + m
  * (q <= n + m), over rows a stride of m. */
 
-/* One round of the MALP-A / MALP-B search (Algorithm 3, lines 5-10, with
- * Algorithm 2 per check) at u[nframes x n]. active[nframes x m] marks
+/* One round of the MALP-A / MALP-B cut search (the search step of
+ * Algorithm 3, with Algorithm 2 per check) at u[nframes x n]. active[nframes x m] marks
  * checks whose inequality is active in the current LP. mask and in_lp are
  * updated in place; flag[nframes] = 1 if an inequality was added. */
 int32_t lpdec_cut_search_device(lpdec_ctx* ctx, const lpdec_code* code,
@@ -286,6 +286,11 @@ int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code,
  *   - Every call uses the same array and leaves its contents behind; the
  *     call resets what must start at zero itself. Calls that overlap on the
  *     GPU (other streams, other threads) race on the array: serialize them.
+ *   - The dense Cholesky fallback of stalled Newton solves is off here
+ *     (its m x m matrices do not fit the array): a frame whose PCG stalls
+ *     continues with the PCG direction, as the regular entry did before
+ *     that fallback, and may end LPDEC_ERR_NOT_CONVERGED where the regular
+ *     entry converges.
  *   - Returns LPDEC_ERR_OUT_OF_BUDGET when one frame's workspace exceeds the
  *     array (very long codes), LPDEC_ERR_INVALID_ARG for bad arguments. */
 int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
