@@ -288,9 +288,8 @@ int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code,
  *     GPU (other streams, other threads) race on the array: serialize them.
  *   - The dense Cholesky fallback of stalled Newton solves is off here
  *     (its m x m matrices do not fit the array): a frame whose PCG stalls
- *     continues with the PCG direction, as the regular entry did before
- *     that fallback, and may end LPDEC_ERR_NOT_CONVERGED where the regular
- *     entry converges.
+ *     continues with the PCG direction and may end LPDEC_ERR_NOT_CONVERGED
+ *     where the regular entry converges.
  *   - Returns LPDEC_ERR_OUT_OF_BUDGET when one frame's workspace exceeds the
  *     array (very long codes), LPDEC_ERR_INVALID_ARG for bad arguments. */
 int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
