@@ -533,7 +533,7 @@ int32_t lpdec_ctx_create(int32_t device, const lpdec_params* params, size_t hbm_
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, device));
     if (prop.major < 10) {
-        snprintf(g_err, sizeof g_err, "device %d is sm_%d%d; this build targets sm_103a",
+        snprintf(g_err, sizeof g_err, "device %d is sm_%d%d; the library is compiled for sm_103a",
                  device, prop.major, prop.minor);
         return LPDEC_ERR_NO_DEVICE;
     }
