@@ -179,7 +179,11 @@ int32_t lpdec_ctx_set_params(lpdec_ctx* ctx, const lpdec_params* params);
 /* Uploads H (m x n) given in CSR form on the host: row_ptr[m+1],
  * col_idx[row_ptr[m]] with strictly increasing columns in each row.
  * Validates the CSR, that every row has 1..32 entries and that
- * m, n <= 32767 (the kernels pack indices into 15 bits). */
+ * m, n <= 32767 (the kernels pack indices into 15 bits). Decoding further
+ * needs the arrays that always live in shared memory (about 12 bytes per
+ * check plus one bit per column, see lpdec_workspace_bytes) to fit one
+ * CTA's shared memory (227 KB): m up to about 18,000. Larger codes are
+ * rejected by the decode calls with LPDEC_ERR_INVALID_ARG. */
 int32_t lpdec_code_create(lpdec_ctx* ctx, int32_t m, int32_t n,
                           const int32_t* row_ptr, const int32_t* col_idx,
                           lpdec_code** out);

@@ -119,3 +119,13 @@ def test_server_reports_missing_device_and_null_handles(lib):
         rc = lib.lpdec_server_create(0, ctypes.byref(bad), 1, 2, rp.ctypes.data, ci.ctypes.data,
                                      lanes, batch, pend, ctypes.byref(out))
         assert rc == L.LPDEC_ERR_INVALID_ARG
+
+
+def test_largest_decodable_sizes(lib):
+    """The always-shared arrays (~12 B per check + 1 bit per column) bound
+    the decodable size: a 16383 x 32767 code fits one CTA's 227 KB of shared
+    memory, a 32767 x 32767 one does not (its decode calls are rejected)."""
+    cap = 227 * 1024
+    assert L.lpdec_workspace_bytes(16383, 32767, 3 * 32767, 0, 0)[1] <= cap
+    assert L.lpdec_workspace_bytes(32767, 32767, 3 * 32767, 0, 0)[1] > cap
+    assert L.lpdec_workspace_bytes(1, 1, 1, 0, 0)[0] == 0          # smallest code
