@@ -11,12 +11,23 @@ MALP-A (Section III-A):
      one. If anything was added, solve the LP to get u^k. Stop when nothing
      was added; u^k is the LP decoding solution.
   Theorem 2(b) makes the cost gamma'u^k strictly increasing when every LP
-  optimum is unique; a cost that does not rise (by more than tau_inc,
-  relative) ends the frame with status STALLED instead of letting the loop
-  cycle between cut sets.
+  optimum is unique. When the cost does not rise (by more than tau_inc,
+  relative), that hypothesis has failed: the optimum is not unique (or not
+  numerically unique), and MALP's removal of inactive inequalities can then
+  cycle between cut sets without reaching the LP decoding optimum. The frame
+  then continues as ALP (Algorithm 1) from its current cut set: from there on
+  nothing is removed and every check is searched. ALP only adds
+  inequalities, so the cost cannot fall and no cut set repeats; it stops
+  when no parity inequality is violated, i.e. at a point of the fundamental
+  polytope that is optimal for a relaxation of it: the LP decoding optimum
+  (Theorem 2(c) for ALP needs no uniqueness).
   MALP-B moves the removal to the start of the round: every inactive
   inequality is dropped before the search. ALP never removes anything and
   searches every check.
+
+LP rows are the cut list ordered by check, and, within a check, by the
+order in which its inequalities were added (a reordering of rows does not
+change the LP).
 
 An inequality is active when its slack x_{n+j} is zero (Section III-A). Each
 LP is solved by ``ipm.solve`` on the augmented form of ``lp.build``; the
@@ -42,7 +53,7 @@ from . import cuts as _cuts
 from . import ipm as _ipm
 from . import lp as _lp
 from . import vertex as _vertex
-from .params import OracleParams, OK, NOT_CONVERGED, STALLED
+from .params import OracleParams, OK, NOT_CONVERGED
 
 
 @dataclasses.dataclass
@@ -73,6 +84,8 @@ class DecodeResult:
     history: list              # LPRecord per LP solved
     cuts: list                 # final cut list (ALP keeps several per check)
     vertex_failures: int = 0   # LPs whose vertex recovery was rejected
+    alp_switch: int = 0        # LPs solved before a MALP frame continued as
+                               # ALP (0: it never did)
 
 
 def hard_decision(gamma: np.ndarray) -> np.ndarray:
@@ -99,9 +112,11 @@ def decode(code, gamma, params: OracleParams | None = None,
     u = hard_decision(gamma)
     cost = float(np.dot(gamma, u))      # gamma'u^0
     in_lp = np.zeros(m, dtype=bool)
-    masks = np.zeros(m, dtype=np.uint32)
-    slack = np.full(m, np.inf)         # slack of check j's inequality
-    alp_cuts = []                      # ALP: ordered cut list
+    masks = np.zeros(m, dtype=np.uint32)   # V of check j's (latest) inequality
+    slack = np.full(m, np.inf)         # least slack over check j's inequalities
+    cuts = []                          # cut list (check, mask) in insertion order
+    alp = prm.variant == "alp"         # ALP semantics (from the start, or after a stall)
+    alp_switch = 0
     history = []
     status = OK
     ipm_total = 0
@@ -109,31 +124,32 @@ def decode(code, gamma, params: OracleParams | None = None,
     vfail = 0
     while True:
         flag = False
-        if prm.variant == "malp_b":
+        if prm.variant == "malp_b" and not alp:
             drop = in_lp & (slack > prm.tau_act)
             in_lp[drop] = False
             masks[drop] = 0
         for j in range(m):
-            if prm.variant != "alp" and in_lp[j] and slack[j] <= prm.tau_act:
+            if not alp and in_lp[j] and slack[j] <= prm.tau_act:
                 continue                # j has an active inequality
             mask, lhs, violated = _cuts.find_violated(u[code.row(j)], prm.tau_cut)
             if violated:
                 flag = True
-                if prm.variant == "alp":
-                    alp_cuts.append((j, mask))
-                    in_lp[j] = True
+                if alp:
+                    cuts.append((j, mask))
                 else:
-                    in_lp[j] = True     # replaces j's old inequality, if any
-                    masks[j] = mask
+                    cuts = [c for c in cuts if c[0] != j]   # replaces j's old inequality
+                    cuts.append((j, mask))
+                in_lp[j] = True
+                masks[j] = mask
+        if not alp:
+            cuts = [c for c in cuts if in_lp[c[0]]]         # MALP-B drops
         if not flag:
             break
         if lps >= prm.max_alp:
             status = NOT_CONVERGED
             break
-        if prm.variant == "alp":
-            lp = _lp.build_from_cuts(code, gamma, alp_cuts)
-        else:
-            lp = _lp.build(code, gamma, in_lp, masks)
+        order = sorted(range(len(cuts)), key=lambda t: (cuts[t][0], t))
+        lp = _lp.build_from_cuts(code, gamma, [cuts[t] for t in order])
         solver = solve_normal_factory(lp.A) if solve_normal_factory else None
         res = _ipm.solve(lp.A, lp.b, lp.c, prm, solve_normal=solver)
         lps += 1
@@ -143,13 +159,8 @@ def decode(code, gamma, params: OracleParams | None = None,
         u = lp.u_from_x(xv)
         s_rows = xv[n:]
         slack = np.full(m, np.inf)
-        if prm.variant == "alp":
-            # several inequalities per check: a check counts as active if
-            # any of its inequalities is active
-            for r, j in enumerate(lp.rows):
-                slack[j] = min(slack[j], s_rows[r])
-        else:
-            slack[lp.rows] = s_rows
+        for r, j in enumerate(lp.rows):   # a check is active if any of its rows is
+            slack[j] = min(slack[j], s_rows[r])
         history.append(LPRecord(p=lp.p, objective=float(np.dot(gamma, u)),
                                 ipm_iters=res.iters, u=u.copy(),
                                 in_lp=in_lp.copy(), masks=masks.copy(),
@@ -158,18 +169,17 @@ def decode(code, gamma, params: OracleParams | None = None,
             status = NOT_CONVERGED
             break
         new_cost = history[-1].objective
-        if new_cost - cost <= prm.tau_inc * (1.0 + abs(cost)):
-            status = STALLED
-            break
+        if not alp and new_cost - cost <= prm.tau_inc * (1.0 + abs(cost)):
+            alp = True                  # Theorem 2(b) fails: continue as ALP
+            alp_switch = lps
         cost = new_cost
     hard, cert = outputs(u, gamma, prm.tau_int)
     out_masks = np.where(in_lp, masks, 0).astype(np.uint32)
-    final_cuts = alp_cuts if prm.variant == "alp" else \
-        [(int(j), int(masks[j])) for j in np.flatnonzero(in_lp)]
+    order = sorted(range(len(cuts)), key=lambda t: (cuts[t][0], t))
     return DecodeResult(u=u, hard=hard, cert=cert, in_lp=in_lp.copy(),
                         masks=out_masks, alp_iters=lps,
                         ipm_iters_total=ipm_total,
                         lp_rows_final=history[-1].p if history else 0,
                         objective=float(np.dot(gamma, u)), status=status,
-                        history=history, cuts=final_cuts,
-                        vertex_failures=vfail)
+                        history=history, cuts=[cuts[t] for t in order],
+                        vertex_failures=vfail, alp_switch=alp_switch)

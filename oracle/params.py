@@ -27,8 +27,8 @@ tests pass identical values to both sides explicitly.
             an LP's cost does not exceed the previous one by more than
             tau_inc * (1 + |previous cost|), that hypothesis has failed (a
             tie or a numerically non-unique optimum, where MALP can cycle
-            between two cut sets) and the frame ends with status STALLED,
-            keeping the last LP's solution.
+            between two cut sets without reaching the optimum) and the frame
+            continues as ALP (Algorithm 1) from its current cut set.
   max_alp, max_ipm, max_pcg: iteration caps; reaching one ends the frame
             with status NOT_CONVERGED.
 """
@@ -40,7 +40,6 @@ import dataclasses
 # frame status codes (same values as the C library's LPDEC_* codes)
 OK = 0
 NOT_CONVERGED = -3
-STALLED = -8
 
 
 @dataclasses.dataclass

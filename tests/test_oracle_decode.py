@@ -171,25 +171,45 @@ def test_initial_lp_is_hard_decision_and_codeword_input():
 
 
 def test_stall_rule_follows_theorem_2b():
-    """Theorem 2(b): the LP cost rises strictly from one LP to the next. A
-    required rise larger than any real one stops the frame right after its
-    first LP with status STALLED and that LP's solution; the default
-    tau_inc never stops a frame of the n=120 workload."""
-    from oracle.params import STALLED
+    """Theorem 2(b): the LP cost rises strictly from one LP to the next
+    (default tau_inc never switches a frame of the n=120 workload to ALP).
+    A required rise larger than any real one switches every frame that needs
+    an LP to ALP (Algorithm 1) after its first LP, and ALP still ends at the
+    LP decoding optimum (Theorem 2(c)): Feldman's full LP."""
     code = named_code("gallager_120")
     G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(40))
     needs_lp = []
     for g in G:
         r = oracle.decode(code, g)
-        assert r.status == 0
+        assert r.status == 0 and r.alp_switch == 0
         costs = [float(np.dot(g, oracle.malp.hard_decision(g)))] + [h.objective for h in r.history]
         assert all(b > a for a, b in zip(costs, costs[1:]))
         if r.alp_iters > 1:
             needs_lp.append(g)
     assert needs_lp
-    r = oracle.decode(code, needs_lp[0], OracleParams(tau_inc=1e6))
-    assert r.status == STALLED and r.alp_iters == 1
-    assert np.array_equal(r.u, r.history[0].u)
+    for g in needs_lp[:3]:
+        r = oracle.decode(code, g, OracleParams(tau_inc=1e6))
+        assert r.status == 0 and r.alp_switch == 1
+        u_ref, f_ref = feldman.lp_decode(code, g)
+        assert abs(r.objective - f_ref) <= 1e-9 * (1 + abs(f_ref))
+        assert np.max(np.abs(r.u - u_ref)) < 1e-7
+
+
+def test_malp_cycle_resolved_by_alp_reaches_full_lp():
+    """Frame 8718 of the (3,6) PEG n=1008 workload at 2 dB: MALP-A's cost
+    stops rising (it alternates between two cut sets, -1.873606357 and
+    -1.873604507, 1.2% below the optimum), so Theorem 2(b)'s uniqueness
+    hypothesis fails there. Continued as ALP the frame reaches Feldman's full
+    LP optimum (Theorem 2(c); HiGHS on all 504 x 32 parity inequalities)."""
+    code = named_code("peg_1008")
+    g = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, [8718])[0]
+    r = oracle.decode(code, g)
+    assert r.status == 0 and r.alp_switch > 0 and r.cert == 0
+    u_ref, f_ref = feldman.lp_decode(code, g)
+    assert abs(r.objective - f_ref) <= 1e-9 * (1 + abs(f_ref))
+    assert np.max(np.abs(r.u - u_ref)) < 1e-7
+    # the MALP-A part alone stops 1.2% below it
+    assert r.history[r.alp_switch - 1].objective < f_ref - 0.01 * abs(f_ref)
 
 
 def test_theorem_2d_each_lp_solves_lp_decoding_of_its_active_checks():
