@@ -48,17 +48,19 @@ extern "C" {
 /* Status codes (return values and lpdec_stats.status). */
 #define LPDEC_OK                 0
 #define LPDEC_ERR_INVALID_ARG   -1  /* bad size, CSR, degree > 32, non-finite gamma */
-#define LPDEC_ERR_OUT_OF_BUDGET -2  /* request exceeds the context's HBM budget */
+#define LPDEC_ERR_OUT_OF_BUDGET -2  /* request exceeds the context's HBM budget; per frame:
+                                       the LP outgrew its row capacity (lp_rows_cap) */
 #define LPDEC_ERR_NOT_CONVERGED -3  /* an iteration cap was reached (per frame) */
 #define LPDEC_ERR_TIMEOUT       -4  /* a bounded wait expired */
 #define LPDEC_ERR_PENDING       -5  /* result not ready yet */
 #define LPDEC_ERR_CUDA          -6  /* a CUDA runtime call failed */
 #define LPDEC_ERR_NO_DEVICE     -7  /* no CUDA device / unsupported architecture */
-#define LPDEC_ERR_STALLED       -8  /* the LP cost stopped rising (per frame; see tau_inc) */
 
-/* Adaptive-LP variants (Section III-A). */
+/* Adaptive-LP variants (Section III-A, Algorithm 1). */
 #define LPDEC_MALP_A 0
 #define LPDEC_MALP_B 1
+#define LPDEC_ALP    2   /* Algorithm 1: inequalities are only added; every check
+                            is searched in every round */
 
 /* Arithmetic of the PCG solve (the IPM state is always FP64). */
 #define LPDEC_FP64  0   /* FP64 PCG */
@@ -88,13 +90,15 @@ extern "C" {
  *   tau_act  = 1e-9   an inequality is active iff its slack <= tau_act
  *   tau_cut  = 1e-9   a check is violated iff Eq. 6's left side < 1 - tau_cut
  *   tau_int  = 1e-9   u is integral iff max |u_i - round(u_i)| <= tau_int
- *   tau_inc  = 1e-9   Theorem 2(b): with unique LP optima the cost gamma'u
- *                     rises strictly from LP to LP. A frame whose new LP cost
- *                     is not above the previous one by more than
- *                     tau_inc * (1 + |previous|) ends with LPDEC_ERR_STALLED
- *                     (an optimum that is not unique, where the adaptive loop
- *                     can cycle between two cut sets), keeping the last LP's
- *                     solution.
+ *   tau_inc  = 1e-9   Theorem 2(b): with unique LP optima the MALP cost
+ *                     gamma'u rises strictly from LP to LP. A MALP frame whose
+ *                     new LP cost is not above the previous one by more than
+ *                     tau_inc * (1 + |previous|) has an optimum that is not
+ *                     unique, where MALP can cycle between cut sets short of
+ *                     the LP decoding optimum; it continues as ALP
+ *                     (Algorithm 1) from its cut set, which only adds
+ *                     inequalities and reaches the optimum (Theorem 2(c);
+ *                     stats.alp_switch records when).
  *   max_alp = 200, max_ipm = 60, max_pcg = 1000 iteration caps (max_pcg per
  *                     Newton solve, over all refinement rounds; an LP whose
  *                     interior-point run converges needs at most ~40
@@ -105,6 +109,10 @@ extern "C" {
  *                     A D^2 A' (LPs of up to 2048 rows), and so are the
  *                     remaining Newton solves of that LP
  *   variant = LPDEC_MALP_A, precision = LPDEC_FP64
+ *   lp_rows_cap = 0   rows one frame's LP may hold (0 = m + m/8 for MALP,
+ *                     whose LPs hold at most one inequality per check until a
+ *                     switch to ALP, and 2m for ALP); a frame whose cut list
+ *                     outgrows it ends with LPDEC_ERR_OUT_OF_BUDGET
  * The decisions are taken on the LP's optimal vertex, recovered from the
  * final interior-point iterate through its strictly complementary
  * partition (basic iff x_i > z_i, Section VI-A) and certified optimal by a
@@ -120,12 +128,13 @@ typedef struct lpdec_params {
     int32_t max_alp, max_ipm, max_pcg, variant, precision;
     int32_t threads_per_block;  /* 0 = library choice */
     int32_t smem_budget;        /* bytes of shared memory per CTA, 0 = library choice */
-    int32_t reserved;
+    int32_t lp_rows_cap;        /* LP row capacity per frame, 0 = library choice */
+    int32_t reserved[3];
 } lpdec_params;
 
 /* Per-frame results besides u / hard / cert. */
 typedef struct lpdec_stats {
-    int32_t status;           /* LPDEC_OK, or LPDEC_ERR_NOT_CONVERGED / STALLED / INVALID_ARG */
+    int32_t status;           /* LPDEC_OK, or LPDEC_ERR_NOT_CONVERGED / OUT_OF_BUDGET / INVALID_ARG */
     int32_t alp_iters;        /* number of LPs solved (0 if the hard decision is a codeword) */
     int32_t ipm_iters_total;  /* interior-point iterations over all LPs */
     int32_t pcg_iters_total;  /* PCG iterations over all Newton steps */
@@ -134,7 +143,7 @@ typedef struct lpdec_stats {
     int32_t max_levels;       /* deepest triangular-solve level schedule seen */
     int32_t pcg_iters_fp64;   /* PCG iterations run in FP64 (all of them in LPDEC_FP64) */
     int32_t dense_solves;     /* Newton systems solved by the dense Cholesky fallback */
-    int32_t reserved;
+    int32_t alp_switch;       /* LPs solved before a MALP frame continued as ALP (0: never) */
     double  objective;        /* gamma'u */
     double  pcg_flops;        /* algorithmic floating-point operations of the Newton
                                  solves: PCG iterations (Q h, both triangular
@@ -142,6 +151,12 @@ typedef struct lpdec_stats {
                                  refinement and any dense fallback */
     double  seconds;          /* device time from the frame's start to its end
                                  (batch entry points: its time on its CTA) */
+    double  pcg_bytes;        /* algorithmic bytes of the PCG iterations of a
+                                 frame streamed from memory: per iteration, both
+                                 index passes and D^2 of Q h (4-byte indices),
+                                 its two vectors, the two triangular solves
+                                 (4 nnz(A_M) + 8p each) and five 8p vector passes */
+    double  t_start, t_end;   /* device global timer (ns) at the frame's start and end */
 } lpdec_stats;
 
 typedef struct lpdec_ctx lpdec_ctx;    /* opaque: device, streams, scratch */
@@ -154,10 +169,11 @@ void lpdec_default_params(lpdec_params* p);
 const char* lpdec_error_string(int32_t code);
 
 /* Host-only (no device needed): the per-frame workspace of a code with m
- * checks, n bits and E edges in the given precision mode — shared memory
- * per CTA (*smem_bytes) and global scratch per concurrently decoded frame
- * (*global_bytes_per_frame, including the dense fallback's m x m FP64
- * matrix when m <= 2048) — for a shared-memory budget per CTA
+ * checks, n bits and E edges (check degrees at most ceil(E/m)) in the given
+ * precision mode, with the default parameters — shared memory per CTA
+ * (*smem_bytes) and global scratch per concurrently decoded frame
+ * (*global_bytes_per_frame, including the dense fallback's matrix when the
+ * LP row capacity is <= 2048) — for a shared-memory budget per CTA
  * (smem_budget <= 0: 227 KB, the largest layout; the decoder itself
  * defaults to a third of the SM's shared memory, 75 KB on GB300). Also
  * validates the layout (every array aligned, inside its region, disjoint
@@ -181,9 +197,11 @@ int32_t lpdec_ctx_set_params(lpdec_ctx* ctx, const lpdec_params* params);
  * Validates the CSR, that every row has 1..32 entries and that
  * m, n <= 32767 (the kernels pack indices into 15 bits). Decoding further
  * needs the arrays that always live in shared memory (about 12 bytes per
- * check plus one bit per column, see lpdec_workspace_bytes) to fit one
- * CTA's shared memory (227 KB): m up to about 18,000. Larger codes are
- * rejected by the decode calls with LPDEC_ERR_INVALID_ARG. */
+ * LP row of capacity, m + m/8 by default, plus one bit per column, see
+ * lpdec_workspace_bytes) to fit one CTA's shared memory (227 KB): m up to
+ * about 16,000. Larger codes are rejected by the decode calls with
+ * LPDEC_ERR_INVALID_ARG. The code may be used with any context on the same
+ * device. */
 int32_t lpdec_code_create(lpdec_ctx* ctx, int32_t m, int32_t n,
                           const int32_t* row_ptr, const int32_t* col_idx,
                           lpdec_code** out);
@@ -195,22 +213,48 @@ int32_t lpdec_decode(lpdec_ctx* ctx, const lpdec_code* code, const double* gamma
                      double* u_out, uint8_t* hard_out, int32_t* cert_out,
                      uint32_t* cut_mask_out, lpdec_stats* stats);
 
+/* Decodes a batch of frames, each with its own code (the problem statement
+ * of Section II-A/B per frame: H and gamma in; u, hard decision and ML
+ * certificate out). Host pointers, one per frame: codes[f] (a code of any
+ * context on this context's device), gammas[f][n_f] in; u_out[f][n_f],
+ * hard_out[f][n_f], cert_out[nframes] out; cut_mask_out (NULL, or one
+ * pointer per frame, each NULL or [m_f]) and stats[nframes] optional. All
+ * frames, whatever their code lengths, share one persistent launch; the
+ * call packs them, copies in and out, and returns when the outputs are
+ * written. Returns LPDEC_ERR_INVALID_ARG for a NULL pointer, a non-finite
+ * LLR or a code of another device; per-frame failures are in stats. */
+int32_t lpdec_decode_batch(lpdec_ctx* ctx, int32_t nframes, const lpdec_code* const* codes,
+                           const double* const* gammas, double* const* u_out,
+                           uint8_t* const* hard_out, int32_t* cert_out,
+                           uint32_t* const* cut_mask_out, lpdec_stats* stats);
+
 /* Decodes nframes frames of one code (host pointers, frame-major):
  * gamma[nframes x n] in; u_out[nframes x n], hard_out[nframes x n],
  * cert_out[nframes] out; cut_mask_out[nframes x m] and stats[nframes]
  * optional. Copies in and out inside the call. */
-int32_t lpdec_decode_batch(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
-                           const double* gamma, double* u_out, uint8_t* hard_out,
-                           int32_t* cert_out, uint32_t* cut_mask_out,
-                           lpdec_stats* stats);
+int32_t lpdec_decode_frames(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                            const double* gamma, double* u_out, uint8_t* hard_out,
+                            int32_t* cert_out, uint32_t* cut_mask_out, lpdec_stats* stats);
 
-/* Same as lpdec_decode_batch with DEVICE pointers, asynchronous on
+/* Same as lpdec_decode_frames with DEVICE pointers, asynchronous on
  * `stream`. d_cut_mask and d_stats may be NULL. One persistent kernel
  * decodes all frames; CTAs take frames from a queue. */
 int32_t lpdec_decode_batch_device(lpdec_ctx* ctx, const lpdec_code* code,
                                   int32_t nframes, const double* d_gamma,
                                   double* d_u, uint8_t* d_hard, int32_t* d_cert,
                                   uint32_t* d_cut_mask, lpdec_stats* d_stats,
+                                  void* stream);
+
+/* Device form of lpdec_decode_batch, asynchronous on `stream`: codes is a
+ * HOST array of nframes code handles; the device arrays are ragged and
+ * frame-major: frame f's bits start at n_0 + ... + n_{f-1} in d_gamma, d_u,
+ * d_hard, its checks at m_0 + ... + m_{f-1} in d_cut_mask (optional), and
+ * d_cert / d_stats (optional) hold one entry per frame. The code table and
+ * frame descriptors are copied to the context's device buffer on `stream`;
+ * the workspace is laid out for the largest code of the batch. */
+int32_t lpdec_decode_mixed_device(lpdec_ctx* ctx, int32_t nframes, const lpdec_code* const* codes,
+                                  const double* d_gamma, double* d_u, uint8_t* d_hard,
+                                  int32_t* d_cert, uint32_t* d_cut_mask, lpdec_stats* d_stats,
                                   void* stream);
 
 /* ---- Single steps of the hot path (device pointers, asynchronous) ----
@@ -285,15 +329,18 @@ int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code,
  *     not used.
  *   - Inputs and outputs are caller-owned device buffers, as in
  *     lpdec_decode_batch_device; asynchronous on `stream`.
- *   - The first call on a device takes the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call takes the array's device address (cudaGetSymbolAddress,
+ *     which allocates nothing); the first call on a device may also load the
+ *     module, so make it before any stream capture.
  *   - Every call uses the same array and leaves its contents behind; the
  *     call resets what must start at zero itself. Calls that overlap on the
  *     GPU (other streams, other threads) race on the array: serialize them.
- *   - The dense Cholesky fallback of stalled Newton solves is off here
- *     (its m x m matrices do not fit the array): a frame whose PCG stalls
- *     continues with the PCG direction and may end LPDEC_ERR_NOT_CONVERGED
- *     where the regular entry converges.
+ *   - The dense Cholesky fallback of stalled Newton solves runs as in the
+ *     regular entry whenever one CTA's workspace with its matrix fits the
+ *     array (n = 1008: about 2.8 MB per CTA, so 11 CTAs run at once instead
+ *     of the regular entry's 456); only codes whose matrix alone outgrows the
+ *     array run without it, and a frame whose PCG stalls there may end
+ *     LPDEC_ERR_NOT_CONVERGED where the regular entry converges.
  *   - Returns LPDEC_ERR_OUT_OF_BUDGET when one frame's workspace exceeds the
  *     array (very long codes), LPDEC_ERR_INVALID_ARG for bad arguments. */
 int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,

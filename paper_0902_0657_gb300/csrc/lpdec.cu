@@ -55,26 +55,47 @@ __device__ __forceinline__ int next_frame(Blk& B, int* counter, int* slot) {
     if (threadIdx.x == 0) ks.sw = serial_warp(B.nwarps);                        \
     __syncthreads();                                                            \
     B.sw = ks.sw;                                                               \
-    WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.gbytes, C0.n, C0.m,      \
-                         (int)L.q2);                                            \
-    const CodeView C = bind_code<T>(C0, W);
+    WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.gbytes);
 
+// Where frame f of a batch lives: its code (index into the batch's code
+// table) and the offsets of its bits and checks in the packed (ragged)
+// frame-major arrays.
+struct FrameDesc {
+    int32_t code;
+    int32_t pad;
+    long long on, om;
+};
+
+// Whole-frame decode. One code for every frame (descs == nullptr; frame f at
+// f*n / f*m), or per-frame codes from codes[descs[f].code] with ragged
+// offsets.
 template <typename T>
 __global__ void __launch_bounds__(512)
-k_decode(CodeView C0, DevParams P, Layout L, const double* __restrict__ gamma,
-         double* u, uint8_t* hard, int32_t* cert, uint32_t* mask, lpdec_stats* stats,
-         int nframes, int* counter, char* gscratch) {
+k_decode(CodeView C0, const CodeView* __restrict__ codes, const FrameDesc* __restrict__ descs,
+         DevParams P, Layout L, const double* __restrict__ gamma, double* u, uint8_t* hard,
+         int32_t* cert, uint32_t* mask, lpdec_stats* stats, int nframes, int* counter,
+         char* gscratch) {
     KERNEL_PROLOGUE
+    CodeView C = descs ? C0 : bind_code<T>(C0, W);
+    int bound = -1;
     for (;;) {
         int f = next_frame(B, counter, &ks.next);
         if (f >= nframes) break;
-        FrameOut o{u + (size_t)f * C.n, hard + (size_t)f * C.n, cert + f,
-                   mask ? mask + (size_t)f * C.m : nullptr, stats ? stats + f : nullptr};
-        decode_frame<T>(B, C, W, P, gamma + (size_t)f * C.n, o, (int)L.q2, ks.shscan);
+        long long on = (long long)f * C0.n, om = (long long)f * C0.m;
+        if (descs) {
+            const FrameDesc d = descs[f];
+            if (d.code != bound) { C = bind_code<T>(codes[d.code], W); bound = d.code; }
+            on = d.on;
+            om = d.om;
+        }
+        FrameOut o{u + on, hard + on, cert + f, mask ? mask + om : nullptr,
+                   stats ? stats + f : nullptr};
+        decode_frame<T>(B, C, W, P, gamma + on, o, 0, ks.shscan);
     }
 }
 
-// flip bits from gamma, flags/mask from the caller's LP state
+// LP state of the step kernels: one inequality per check (in_lp, mask),
+// flip bits from gamma; the next lp_build makes the cut list from it.
 template <typename T>
 __device__ inline void load_lp_state(Blk& B, const CodeView& C, WS<T>& W, const double* g,
                                      const uint8_t* in_lp, const uint32_t* mask) {
@@ -87,9 +108,10 @@ __device__ inline void load_lp_state(Blk& B, const CodeView& C, WS<T>& W, const 
         W.flip[k] = bits;
     }
     for (int j = B.tid; j < C.m; j += B.nt) {
-        W.flags[j] = in_lp[j] ? kInLP : 0;
+        W.flags[j] = in_lp[j] ? (kInLP | kNew) : 0;
         W.mask[j] = mask[j];
     }
+    for (int j = B.tid; j <= C.m; j += B.nt) W.crptr[j] = 0;
     __syncthreads();
 }
 
@@ -99,6 +121,7 @@ k_cut_search(CodeView C0, DevParams P, Layout L, const double* u, const uint8_t*
              uint8_t* in_lp, uint32_t* mask, int32_t* flag, int nframes, int* counter,
              char* gscratch) {
     KERNEL_PROLOGUE
+    const CodeView C = bind_code<T>(C0, W);
     for (;;) {
         int f = next_frame(B, counter, &ks.next);
         if (f >= nframes) break;
@@ -112,7 +135,7 @@ k_cut_search(CodeView C0, DevParams P, Layout L, const double* u, const uint8_t*
         }
         __syncthreads();
         if (P.variant == LPDEC_MALP_B) drop_inactive<T>(B, C, W);
-        int added = cut_search<T>(B, C, W, P);
+        int added = cut_search<T>(B, C, W, P, P.variant == LPDEC_ALP);
         for (int j = B.tid; j < C.m; j += B.nt) {
             in_lp[om + j] = (W.flags[j] & kInLP) ? 1 : 0;
             mask[om + j] = W.mask[j];
@@ -128,6 +151,7 @@ k_mts_select(CodeView C0, DevParams P, Layout L, const double* gamma, const uint
              const uint32_t* mask, const double* wts, int32_t* col, int32_t* row,
              int nframes, int* counter, char* gscratch) {
     KERNEL_PROLOGUE
+    const CodeView C = bind_code<T>(C0, W);
     const int qm = C.n + C.m;
     for (;;) {
         int f = next_frame(B, counter, &ks.next);
@@ -135,10 +159,10 @@ k_mts_select(CodeView C0, DevParams P, Layout L, const double* gamma, const uint
         load_lp_state<T>(B, C, W, gamma + (size_t)f * C.n, in_lp + (size_t)f * C.m,
                          mask + (size_t)f * C.m);
         Frame F{0, C.n, 0.0, 0.0, 0};
-        lp_build<T>(B, C, W, F, ks.shscan);
+        lp_build<T>(B, C, W, F, ks.shscan, false);
         for (int i = B.tid; i < F.q; i += B.nt) W.d2[i] = wts[(size_t)f * qm + i];
         __syncthreads();
-        mts_select<T>(B, C, W, F, W.d2, (int)L.q2);
+        mts_select<T>(B, C, W, F, W.d2, 0);
         selection_order<T>(B, W, F, col + (size_t)f * C.m, row + (size_t)f * C.m, C.m);
         __syncthreads();
     }
@@ -150,6 +174,7 @@ k_pcg(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in
       const uint32_t* mask, const double* d2, const double* wv, double* dy, int32_t* iters,
       int nframes, int* counter, char* gscratch) {
     KERNEL_PROLOGUE
+    const CodeView C = bind_code<T>(C0, W);
     const int qm = C.n + C.m;
     for (;;) {
         int f = next_frame(B, counter, &ks.next);
@@ -157,11 +182,11 @@ k_pcg(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in
         load_lp_state<T>(B, C, W, gamma + (size_t)f * C.n, in_lp + (size_t)f * C.m,
                          mask + (size_t)f * C.m);
         Frame F{0, C.n, 0.0, 0.0, 0};
-        lp_build<T>(B, C, W, F, ks.shscan);
+        lp_build<T>(B, C, W, F, ks.shscan, false);
         for (int i = B.tid; i < F.q; i += B.nt) W.d2[i] = d2[(size_t)f * qm + i];
         for (int r = B.tid; r < F.p; r += B.nt) W.w[r] = wv[(size_t)f * C.m + r];
         __syncthreads();
-        Levels Lv = mts_select<T>(B, C, W, F, W.d2, (int)L.q2);
+        Levels Lv = mts_select<T>(B, C, W, F, W.d2, 0);
         for (int i = B.tid; i < F.q; i += B.nt) W.d2t[i] = (T)W.d2[i];
         for (int r = B.tid; r < F.p; r += B.nt) W.invd2p[r] = (T)(1.0 / W.d2[W.pivcol[r]]);
         __syncthreads();
@@ -181,6 +206,7 @@ k_lp_solve(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_
            const uint32_t* mask, double* xo, lpdec_stats* stats, int nframes, int* counter,
            char* gscratch, double* trace, int max_trace) {
     KERNEL_PROLOGUE
+    const CodeView C = bind_code<T>(C0, W);
     const int qm = C.n + C.m;
     for (;;) {
         int f = next_frame(B, counter, &ks.next);
@@ -188,10 +214,10 @@ k_lp_solve(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_
         const double* g = gamma + (size_t)f * C.n;
         load_lp_state<T>(B, C, W, g, in_lp + (size_t)f * C.m, mask + (size_t)f * C.m);
         Frame F{0, C.n, 0.0, 0.0, 0};
-        lp_build<T>(B, C, W, F, ks.shscan);
+        lp_build<T>(B, C, W, F, ks.shscan, false);
         lpdec_stats st{};
         if (F.p > 0) {
-            IpmOut io = ipm_solve<T>(B, C, W, F, P, g, (int)L.q2,
+            IpmOut io = ipm_solve<T>(B, C, W, F, P, g, 0,
                                      trace ? trace + (size_t)f * 8 * max_trace : nullptr,
                                      max_trace);
             int ok = io.certified || certify<T>(B, C, W, F, g);
@@ -237,12 +263,20 @@ struct lpdec_ctx {
     int* counter = nullptr;
     char* staging = nullptr;     // device buffers of the host entry points
     size_t staging_bytes = 0;
+    char* h_stage = nullptr;     // pinned host buffer of the host entry points
+    size_t h_stage_bytes = 0;
+    char* d_meta = nullptr;      // code table and frame descriptors of a mixed batch
+    char* h_meta = nullptr;      // ... and their pinned host copy
+    size_t meta_bytes = 0;
+    cudaEvent_t meta_done = nullptr;   // the last copy out of h_meta has run
     std::mutex mu;
 };
 
 struct lpdec_code {
     lpdec_ctx* ctx = nullptr;
+    int device = 0;
     int m = 0, n = 0, E = 0;
+    int dmax = 0;   // largest check degree
     int *h_ptr = nullptr, *h_col = nullptr, *e_chk = nullptr;
     int *v_ptr = nullptr, *v_chk = nullptr, *v_eidx = nullptr;
 };
@@ -273,9 +307,22 @@ DevParams to_dev(const lpdec_params& p) {
     return d;
 }
 
-CodeView view_of(const lpdec_code* c) {
+// LP row capacity of one frame (lp_rows_cap; library choice: m + m/8 for
+// MALP, whose LPs hold one inequality per check until a frame continues as
+// ALP, 2m for ALP). Row indices are packed in 15 bits and column indices
+// n + r in 16.
+int rows_cap(const lpdec_params& prm, int n, int m) {
+    long long cap = prm.lp_rows_cap > 0 ? prm.lp_rows_cap
+                  : (prm.variant == LPDEC_ALP ? 2LL * m : (long long)m + (m + 7) / 8);
+    cap = std::min<long long>({cap, 32767LL, 65535LL - n});
+    return (int)std::max<long long>(cap, 1);
+}
+
+CodeView view_of(const lpdec_code* c, const lpdec_params& prm) {
     CodeView v;
     v.n = c->n; v.m = c->m; v.E = c->E;
+    v.pmax = rows_cap(prm, c->n, c->m);
+    v.eamax = v.pmax * c->dmax;
     v.h_ptr = c->h_ptr; v.h_col = c->h_col; v.e_chk = c->e_chk;
     v.v_ptr = c->v_ptr; v.v_chk = c->v_chk; v.v_eidx = c->v_eidx;
     return v;
@@ -304,43 +351,60 @@ bool layout_ok(const Layout& L, const std::vector<size_t>& sizes) {
     return true;
 }
 
+// Capacities one workspace is laid out for: the largest code of a launch.
+struct Dims {
+    int n = 0, m = 0, pmax = 0, eamax = 0;
+    void cover(const CodeView& v) {
+        n = std::max(n, v.n); m = std::max(m, v.m);
+        pmax = std::max(pmax, v.pmax); eamax = std::max(eamax, v.eamax);
+    }
+};
+
+// Largest LP (rows) for which the dense Cholesky fallback keeps its FP64
+// matrix in per-CTA scratch (32 MB at the limit).
+constexpr int kDenseMaxRows = 2048;
+
 // Lays the workspace out. Hot arrays (everything the PCG loop and the MTS
 // selection touch) go to shared memory in priority order while they fit the
 // budget; the bitmap and the level pointer arrays, which the kernels update
 // with shared-memory atomics, always do. The FP64 interior-point state goes
-// to per-CTA global scratch.
-// Largest LP (rows) for which the dense Cholesky fallback keeps its m x m
-// FP64 matrix in per-CTA scratch (32 MB at the limit).
-constexpr int kDenseMaxRows = 2048;
-
-Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes, bool m32, bool dense) {
-    const size_t q = (size_t)n + m;
+// to per-CTA global scratch. dense_rows = capacity of the dense fallback's
+// matrix (0 = fallback off).
+Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, int dense_rows) {
+    const int n = d.n, m = d.m, pm = d.pmax;
+    const size_t ea = (size_t)std::max(d.eamax, 1);
+    const size_t q = (size_t)n + pm;
     size_t q2 = 1;
     while (q2 < q) q2 <<= 1;
-    const size_t vec = std::max(vec_bytes(n, m, real_bytes, m32), 8 * q2 + 4 * q);
+    const size_t vec = std::max(vec_bytes(n, pm, real_bytes, m32), 8 * q2 + 4 * q);
     struct Spec { int id; size_t bytes; int where; };  // 0 = budgeted, 1 = always shared, 2 = global
-    const size_t D = 8, I = 4, H = 2;
+    const size_t D = 8, I = 4, H = 2, P = (size_t)pm;
     std::vector<Spec> specs = {
-        {S_BITMAP, I * ((q + 31) / 32), 1}, {S_LBPTR, I * (m + 2), 1}, {S_LFPTR, I * (m + 2), 1},
-        {S_CUR, I * (m + 2), 1},
+        {S_BITMAP, I * ((q + 31) / 32), 1}, {S_LBPTR, I * (P + 2), 1}, {S_LFPTR, I * (P + 2), 1},
+        {S_CUR, I * (P + 2), 1},
         // budgeted arrays in priority order: first what every PCG iteration
         // reads on its serial path (the two level-scheduled triangular
         // solves), then the sparse passes of Q h, then what runs once per
-        // interior-point iteration (MTS selection, level build, cut search)
-        {S_VEC, vec, 0}, {S_BDEP, H * E, 0}, {S_FDEP, H * E, 0}, {S_BPTR, I * (m + 1), 0},
-        {S_FPTR, I * (m + 1), 0}, {S_LBROWS, H * m, 0}, {S_LFROWS, H * m, 0},
-        {S_PSGN, (size_t)m, 0}, {S_ROWENT, H * E, 0}, {S_ROWCHK, H * m, 0},
-        {S_HPTR, I * (m + 1), 0}, {S_COLENT, H * E, 0}, {S_VPTR, I * (n + 1), 0},
-        {S_PIVROW, H * q, 0}, {S_PIVCOL, H * m, 0}, {S_CHKROW, H * m, 0}, {S_LB, H * m, 0},
-        {S_LF, H * m, 0}, {S_SELROW, H * m, 0}, {S_DEG, q, 0}, {S_FLAGS, (size_t)m, 0},
-        {S_MASK, I * m, 0}, {S_FLIP, I * ((n + 31) / 32), 0},
-        {G_X, D * q, 2}, {G_Z, D * q, 2}, {G_RC, D * q, 2}, {G_D2, D * q, 2}, {G_Y, D * m, 2},
-        {G_B, D * m, 2}, {G_W, D * m, 2}, {G_DY, D * m, 2}, {G_R64, D * m, 2}, {G_U, D * n, 2},
+        // interior-point iteration (MTS selection, level build), then the
+        // cut search and the cut list
+        {S_VEC, vec, 0}, {S_BDEP, H * ea, 0}, {S_FDEP, H * ea, 0}, {S_BPTR, I * (P + 1), 0},
+        {S_FPTR, I * (P + 1), 0}, {S_LBROWS, H * P, 0}, {S_LFROWS, H * P, 0},
+        {S_PSGN, P, 0}, {S_ROWENT, H * ea, 0}, {S_RPTR, I * (P + 1), 0},
+        {S_COLENT, H * ea, 0}, {S_CPTR, I * ((size_t)n + 1), 0},
+        {S_PIVROW, H * q, 0}, {S_PIVCOL, H * P, 0}, {S_LB, H * P, 0},
+        {S_LF, H * P, 0}, {S_SELROW, H * P, 0}, {S_DEG, H * q, 0},
+        {S_HPTR, I * ((size_t)m + 1), 0}, {S_VPTR, I * ((size_t)n + 1), 0},
+        {S_CCHK, H * P, 0}, {S_CRPTR, I * ((size_t)m + 1), 0}, {S_FLAGS, (size_t)m, 0},
+        {S_MASK, I * (size_t)m, 0}, {S_CMASK, I * P, 0}, {S_CACT, P, 0},
+        {S_FLIP, I * (((size_t)n + 31) / 32), 0},
+        {G_X, D * q, 2}, {G_Z, D * q, 2}, {G_RC, D * q, 2}, {G_D2, D * q, 2}, {G_Y, D * P, 2},
+        {G_B, D * P, 2}, {G_W, D * P, 2}, {G_DY, D * P, 2}, {G_R64, D * P, 2}, {G_U, D * n, 2},
         {G_T64, D * n, 2}, {G_BASIC, q, 2},
         {G_VX, D * q, 2}, {G_V1, D * q, 2}, {G_V2, D * q, 2}, {G_V3, D * q, 2}, {G_V4, D * q, 2},
-        {G_VR1, D * m, 2}, {G_VR2, D * m, 2},
-        {G_P64, real_bytes < 8 ? D * vec_elems(n, m) : 16, 2},
-        {G_QD, dense ? D * (size_t)m * m : 16, 2},
+        {G_VR1, D * P, 2}, {G_VR2, D * P, 2},
+        {G_P64, real_bytes < 8 ? D * vec_elems(n, pm) : 16, 2},
+        {G_QD, dense_rows > 0 ? D * (size_t)dense_rows * dense_rows : 16, 2},
+        {G_CCHK2, H * P, 2}, {G_CMASK2, I * P, 2}, {G_CRPTR2, I * ((size_t)m + 1), 2},
     };
     Layout L{};
     size_t s = 0, g = 0;
@@ -358,11 +422,17 @@ Layout make_layout(int n, int m, int E, size_t budget, size_t real_bytes, bool m
     }
     L.smem_bytes = (uint32_t)s;
     L.q2 = (uint32_t)q2;
-    L.dense = dense ? 1u : 0u;
+    L.dense = (uint32_t)std::max(dense_rows, 0);
+    L.nmax = (uint32_t)n;
+    L.mmax = (uint32_t)m;
+    L.pmax = (uint32_t)pm;
     L.gbytes = align_up(g, 256);
-    if (specs.size() != (size_t)A_COUNT || !layout_ok(L, sizes)) L.smem_bytes = 0xffffffffu;
+    if (specs.size() != (size_t)A_COUNT || !layout_ok(L, sizes) || g >= kGlobalBit)
+        L.smem_bytes = 0xffffffffu;
     return L;
 }
+
+int dense_rows_for(const Dims& d) { return d.pmax <= kDenseMaxRows ? d.pmax : 0; }
 
 struct Launch {
     Layout L;
@@ -370,11 +440,7 @@ struct Launch {
     int grid;
 };
 
-template <typename K>
-int32_t plan(lpdec_ctx* ctx, const lpdec_code* code, int nframes, K kernel, size_t real_bytes,
-             Launch* out) {
-    int threads = ctx->prm.threads_per_block > 0 ? ctx->prm.threads_per_block : 128;
-    threads = std::max(32, std::min(512, threads / 32 * 32));
+size_t smem_budget_of(const lpdec_ctx* ctx) {
     size_t cap = (size_t)ctx->smem_optin - sizeof(KernelShared) - 1024;
     // Library choice: a third of the SM's shared memory per CTA, so that three
     // frames share an SM (the frame's chain of dependent block-wide steps
@@ -383,10 +449,17 @@ int32_t plan(lpdec_ctx* ctx, const lpdec_code* code, int nframes, K kernel, size
     // to global scratch, in the layout's priority order.
     const size_t third = (size_t)ctx->smem_per_sm / 3;
     const size_t per_cta = sizeof(KernelShared) + 1024 + 256;
-    size_t budget = ctx->prm.smem_budget > 0 ? std::min((size_t)ctx->prm.smem_budget, cap)
-                  : (third > per_cta ? std::min(cap, third - per_cta) : cap);
-    Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes,
-                           ctx->prm.precision == LPDEC_M32, code->m <= kDenseMaxRows);
+    return ctx->prm.smem_budget > 0 ? std::min((size_t)ctx->prm.smem_budget, cap)
+         : (third > per_cta ? std::min(cap, third - per_cta) : cap);
+}
+
+template <typename K>
+int32_t plan(lpdec_ctx* ctx, const Dims& dims, int nframes, K kernel, size_t real_bytes,
+             Launch* out) {
+    int threads = ctx->prm.threads_per_block > 0 ? ctx->prm.threads_per_block : 128;
+    threads = std::max(32, std::min(512, threads / 32 * 32));
+    Layout L = make_layout(dims, smem_budget_of(ctx), real_bytes,
+                           ctx->prm.precision == LPDEC_M32, dense_rows_for(dims));
     if (L.smem_bytes == 0xffffffffu) {
         snprintf(g_err, sizeof g_err, "inconsistent workspace layout");
         return LPDEC_ERR_INVALID_ARG;
@@ -421,6 +494,14 @@ int32_t plan(lpdec_ctx* ctx, const lpdec_code* code, int nframes, K kernel, size
     return LPDEC_OK;
 }
 
+template <typename K>
+int32_t plan(lpdec_ctx* ctx, const lpdec_code* code, int nframes, K kernel, size_t real_bytes,
+             Launch* out) {
+    Dims d;
+    d.cover(view_of(code, ctx->prm));
+    return plan(ctx, d, nframes, kernel, real_bytes, out);
+}
+
 int32_t staging(lpdec_ctx* ctx, size_t bytes) {
     if (bytes <= ctx->staging_bytes) return LPDEC_OK;
     if (ctx->budget && bytes + ctx->gscratch_bytes > ctx->budget) return LPDEC_ERR_OUT_OF_BUDGET;
@@ -432,9 +513,44 @@ int32_t staging(lpdec_ctx* ctx, size_t bytes) {
     return LPDEC_OK;
 }
 
+// Device and pinned host buffers for the metadata of a mixed batch (grown,
+// never shrunk; the host copy is reused only after its last copy ran).
+int32_t meta_buffers(lpdec_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->meta_bytes) return LPDEC_OK;
+    if (ctx->meta_done) CK(cudaEventSynchronize(ctx->meta_done));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_meta);
+    cudaFreeHost(ctx->h_meta);
+    ctx->d_meta = ctx->h_meta = nullptr;
+    ctx->meta_bytes = 0;
+    bytes = align_up(bytes * 2, 4096);
+    CK(cudaMalloc(&ctx->d_meta, bytes));
+    CK(cudaMallocHost(&ctx->h_meta, bytes));
+    ctx->meta_bytes = bytes;
+    return LPDEC_OK;
+}
+
+int32_t host_staging(lpdec_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->h_stage_bytes) return LPDEC_OK;
+    cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_bytes = 0;
+    CK(cudaMallocHost(&ctx->h_stage, bytes));
+    ctx->h_stage_bytes = bytes;
+    return LPDEC_OK;
+}
+
+bool params_ok(const lpdec_params& p) {
+    if (p.variant != LPDEC_MALP_A && p.variant != LPDEC_MALP_B && p.variant != LPDEC_ALP)
+        return false;
+    if (p.precision != LPDEC_FP64 && p.precision != LPDEC_MIXED && p.precision != LPDEC_M32)
+        return false;
+    return p.lp_rows_cap >= 0;
+}
+
 int32_t check_ctx_code(lpdec_ctx* ctx, const lpdec_code* code) {
-    if (!ctx || !code || code->ctx != ctx) {
-        snprintf(g_err, sizeof g_err, "null or mismatched context/code");
+    if (!ctx || !code || code->device != ctx->device) {
+        snprintf(g_err, sizeof g_err, "null context/code, or a code of another device");
         return LPDEC_ERR_INVALID_ARG;
     }
     CK(cudaSetDevice(ctx->device));
@@ -450,15 +566,75 @@ int32_t launch_decode(lpdec_ctx* ctx, const lpdec_code* code, int nframes, const
     int32_t rc = mixed ? plan(ctx, code, nframes, k_decode<float>, 4, &ln)
                        : plan(ctx, code, nframes, k_decode<double>, 8, &ln);
     if (rc) return rc;
+    const CodeView cv = view_of(code, ctx->prm);
+    const DevParams dp = to_dev(ctx->prm);
     CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
     if (mixed)
         k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
+            cv, nullptr, nullptr, dp, ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
             nframes, ctx->counter, ctx->gscratch);
     else
         k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
+            cv, nullptr, nullptr, dp, ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
             nframes, ctx->counter, ctx->gscratch);
+    CK(cudaGetLastError());
+    return LPDEC_OK;
+}
+
+// Batch of frames of several codes (ragged frame-major arrays, descriptors
+// built here). The code table and the descriptors go to the context's
+// device buffer through its pinned host buffer, on stream s.
+int32_t launch_decode_mixed(lpdec_ctx* ctx, int nframes, const lpdec_code* const* codes,
+                            const double* d_gamma, double* d_u, uint8_t* d_hard, int32_t* d_cert,
+                            uint32_t* d_mask, lpdec_stats* d_stats, cudaStream_t s) {
+    if (nframes == 0) return LPDEC_OK;
+    std::vector<const lpdec_code*> table;
+    std::vector<FrameDesc> desc((size_t)nframes);
+    Dims dims;
+    long long on = 0, om = 0;
+    for (int f = 0; f < nframes; ++f) {
+        const lpdec_code* c = codes[f];
+        int k = -1;
+        for (size_t t = 0; t < table.size(); ++t)
+            if (table[t] == c) { k = (int)t; break; }
+        if (k < 0) {
+            k = (int)table.size();
+            table.push_back(c);
+            dims.cover(view_of(c, ctx->prm));
+        }
+        desc[f] = FrameDesc{k, 0, on, om};
+        on += c->n;
+        om += c->m;
+    }
+    std::vector<CodeView> views;
+    for (const lpdec_code* c : table) views.push_back(view_of(c, ctx->prm));
+    const size_t vbytes = align_up(views.size() * sizeof(CodeView), 256);
+    const size_t dbytes = desc.size() * sizeof(FrameDesc);
+    int32_t rc = meta_buffers(ctx, vbytes + dbytes);
+    if (rc) return rc;
+    // the pinned buffer may still feed the previous launch's copy
+    CK(cudaEventSynchronize(ctx->meta_done));
+    std::memcpy(ctx->h_meta, views.data(), views.size() * sizeof(CodeView));
+    std::memcpy(ctx->h_meta + vbytes, desc.data(), dbytes);
+    CK(cudaMemcpyAsync(ctx->d_meta, ctx->h_meta, vbytes + dbytes, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(ctx->meta_done, s));
+    Launch ln;
+    const bool mixed = ctx->prm.precision == LPDEC_MIXED;
+    rc = mixed ? plan(ctx, dims, nframes, k_decode<float>, 4, &ln)
+               : plan(ctx, dims, nframes, k_decode<double>, 8, &ln);
+    if (rc) return rc;
+    const CodeView* dv = reinterpret_cast<const CodeView*>(ctx->d_meta);
+    const FrameDesc* dd = reinterpret_cast<const FrameDesc*>(ctx->d_meta + vbytes);
+    const DevParams dp = to_dev(ctx->prm);
+    CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
+    if (mixed)
+        k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+            views[0], dv, dd, dp, ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats, nframes,
+            ctx->counter, ctx->gscratch);
+    else
+        k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+            views[0], dv, dd, dp, ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats, nframes,
+            ctx->counter, ctx->gscratch);
     CK(cudaGetLastError());
     return LPDEC_OK;
 }
@@ -488,19 +664,19 @@ void lpdec_default_params(lpdec_params* p) {
     p->max_pcg = 1000;
     p->variant = LPDEC_MALP_A;
     p->precision = LPDEC_FP64;
+    p->lp_rows_cap = 0;
 }
 
 const char* lpdec_error_string(int32_t code) {
     switch (code) {
         case LPDEC_OK: return "ok";
         case LPDEC_ERR_INVALID_ARG: return "invalid argument";
-        case LPDEC_ERR_OUT_OF_BUDGET: return "out of HBM budget";
+        case LPDEC_ERR_OUT_OF_BUDGET: return "out of HBM budget or LP row capacity";
         case LPDEC_ERR_NOT_CONVERGED: return "iteration cap reached";
         case LPDEC_ERR_TIMEOUT: return "timeout";
         case LPDEC_ERR_PENDING: return "pending";
         case LPDEC_ERR_CUDA: return g_err[0] ? g_err : "CUDA error";
         case LPDEC_ERR_NO_DEVICE: return "no usable CUDA device";
-        case LPDEC_ERR_STALLED: return "LP cost stopped rising (optimum not unique)";
         default: return "unknown status";
     }
 }
@@ -512,8 +688,15 @@ int32_t lpdec_workspace_bytes(int32_t m, int32_t n, int32_t E, int32_t precision
         (precision != LPDEC_FP64 && precision != LPDEC_MIXED && precision != LPDEC_M32))
         return LPDEC_ERR_INVALID_ARG;
     size_t budget = smem_budget > 0 ? (size_t)smem_budget : (size_t)227 * 1024;
-    Layout L = make_layout(n, m, E, budget, precision == LPDEC_MIXED ? 4 : 8,
-                           precision == LPDEC_M32, m <= kDenseMaxRows);
+    lpdec_params prm;
+    lpdec_default_params(&prm);
+    Dims d;
+    d.n = n;
+    d.m = m;
+    d.pmax = rows_cap(prm, n, m);
+    d.eamax = d.pmax * ((E + m - 1) / m);   // check degrees at most ceil(E/m)
+    Layout L = make_layout(d, budget, precision == LPDEC_MIXED ? 4 : 8, precision == LPDEC_M32,
+                           dense_rows_for(d));
     if (L.smem_bytes == 0xffffffffu) return LPDEC_ERR_INVALID_ARG;
     if (smem_bytes) *smem_bytes = L.smem_bytes + sizeof(KernelShared);
     if (global_bytes_per_frame) *global_bytes_per_frame = (size_t)L.gbytes;
@@ -542,11 +725,16 @@ int32_t lpdec_ctx_create(int32_t device, const lpdec_params* params, size_t hbm_
     if (!c) return LPDEC_ERR_INVALID_ARG;
     c->device = device;
     if (params) c->prm = *params; else lpdec_default_params(&c->prm);
+    if (!params_ok(c->prm)) {
+        delete c;
+        return LPDEC_ERR_INVALID_ARG;
+    }
     c->budget = hbm_budget_bytes;
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = (int)prop.sharedMemPerBlockOptin;
     c->smem_per_sm = (int)prop.sharedMemPerMultiprocessor;
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->meta_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&c->counter, sizeof(int)) != cudaSuccess) {
         snprintf(g_err, sizeof g_err, "context allocation failed");
         if (c->stream) cudaStreamDestroy(c->stream);
@@ -561,19 +749,21 @@ void lpdec_ctx_destroy(lpdec_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->meta_done) cudaEventSynchronize(ctx->meta_done);
     cudaFree(ctx->gscratch);
     cudaFree(ctx->staging);
     cudaFree(ctx->counter);
+    cudaFree(ctx->d_meta);
+    cudaFreeHost(ctx->h_meta);
+    cudaFreeHost(ctx->h_stage);
+    if (ctx->meta_done) cudaEventDestroy(ctx->meta_done);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
 
 int32_t lpdec_ctx_set_params(lpdec_ctx* ctx, const lpdec_params* params) {
     if (!ctx || !params) return LPDEC_ERR_INVALID_ARG;
-    if (params->variant != LPDEC_MALP_A && params->variant != LPDEC_MALP_B) return LPDEC_ERR_INVALID_ARG;
-    if (params->precision != LPDEC_FP64 && params->precision != LPDEC_MIXED &&
-        params->precision != LPDEC_M32)
-        return LPDEC_ERR_INVALID_ARG;
+    if (!params_ok(*params)) return LPDEC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> g(ctx->mu);
     ctx->prm = *params;
     return LPDEC_OK;
@@ -591,6 +781,8 @@ int32_t lpdec_code_create(lpdec_ctx* ctx, int32_t m, int32_t n, const int32_t* r
     }
     const int E = row_ptr[m];
     if (E > 0 && !col_idx) return LPDEC_ERR_INVALID_ARG;
+    int dmax = 0;
+    for (int j = 0; j < m; ++j) dmax = std::max(dmax, row_ptr[j + 1] - row_ptr[j]);
     std::vector<int> e_chk(E), vdeg(n + 1, 0);
     for (int j = 0; j < m; ++j) {
         for (int e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
@@ -615,7 +807,9 @@ int32_t lpdec_code_create(lpdec_ctx* ctx, int32_t m, int32_t n, const int32_t* r
     lpdec_code* c = new (std::nothrow) lpdec_code();
     if (!c) return LPDEC_ERR_INVALID_ARG;
     c->ctx = ctx;
+    c->device = ctx->device;
     c->m = m; c->n = n; c->E = E;
+    c->dmax = dmax;
     auto up = [&](int** dst, const int* src, size_t cnt) -> bool {
         if (cudaMalloc(dst, std::max<size_t>(cnt, 1) * sizeof(int)) != cudaSuccess) return false;
         return cnt == 0 || cudaMemcpy(*dst, src, cnt * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -653,9 +847,9 @@ int32_t lpdec_decode_batch_device(lpdec_ctx* ctx, const lpdec_code* code, int32_
                          (cudaStream_t)stream);
 }
 
-int32_t lpdec_decode_batch(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
-                           const double* gamma, double* u_out, uint8_t* hard_out,
-                           int32_t* cert_out, uint32_t* cut_mask_out, lpdec_stats* stats) {
+int32_t lpdec_decode_frames(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                            const double* gamma, double* u_out, uint8_t* hard_out,
+                            int32_t* cert_out, uint32_t* cut_mask_out, lpdec_stats* stats) {
     int32_t rc = check_ctx_code(ctx, code);
     if (rc) return rc;
     if (nframes < 0 || (nframes > 0 && (!gamma || !u_out || !hard_out || !cert_out)))
@@ -694,7 +888,79 @@ int32_t lpdec_decode_batch(lpdec_ctx* ctx, const lpdec_code* code, int32_t nfram
 int32_t lpdec_decode(lpdec_ctx* ctx, const lpdec_code* code, const double* gamma, double* u_out,
                      uint8_t* hard_out, int32_t* cert_out, uint32_t* cut_mask_out,
                      lpdec_stats* stats) {
-    return lpdec_decode_batch(ctx, code, 1, gamma, u_out, hard_out, cert_out, cut_mask_out, stats);
+    return lpdec_decode_frames(ctx, code, 1, gamma, u_out, hard_out, cert_out, cut_mask_out, stats);
+}
+
+// Frames of several codes: checks, packs the per-frame host arrays into the
+// context's pinned buffer, runs one persistent launch over the ragged batch
+// and scatters the results back.
+int32_t lpdec_decode_batch(lpdec_ctx* ctx, int32_t nframes, const lpdec_code* const* codes,
+                           const double* const* gammas, double* const* u_out,
+                           uint8_t* const* hard_out, int32_t* cert_out,
+                           uint32_t* const* cut_mask_out, lpdec_stats* stats) {
+    if (!ctx || nframes < 0) return LPDEC_ERR_INVALID_ARG;
+    if (nframes == 0) return LPDEC_OK;
+    if (!codes || !gammas || !u_out || !hard_out || !cert_out) return LPDEC_ERR_INVALID_ARG;
+    size_t N = 0, M = 0;
+    for (int f = 0; f < nframes; ++f) {
+        int32_t rc = check_ctx_code(ctx, codes[f]);
+        if (rc) return rc;
+        if (!gammas[f] || !u_out[f] || !hard_out[f]) return LPDEC_ERR_INVALID_ARG;
+        for (int i = 0; i < codes[f]->n; ++i)
+            if (!std::isfinite(gammas[f][i])) return LPDEC_ERR_INVALID_ARG;
+        N += codes[f]->n;
+        M += codes[f]->m;
+    }
+    std::lock_guard<std::mutex> g(ctx->mu);
+    const size_t nf = (size_t)nframes;
+    size_t o_g = 0;
+    size_t o_u = align_up(o_g + N * 8, 256);
+    size_t o_h = align_up(o_u + N * 8, 256);
+    size_t o_c = align_up(o_h + N, 256);
+    size_t o_m = align_up(o_c + nf * 4, 256);
+    size_t o_s = align_up(o_m + M * 4, 256);
+    size_t tot = align_up(o_s + nf * sizeof(lpdec_stats), 256);
+    int32_t rc = staging(ctx, tot);
+    if (rc) return rc;
+    rc = host_staging(ctx, tot);
+    if (rc) return rc;
+    char* b = ctx->staging;
+    char* h = ctx->h_stage;
+    cudaStream_t s = ctx->stream;
+    for (size_t f = 0, on = 0; f < nf; on += codes[f]->n, ++f)
+        std::memcpy(h + o_g + on * 8, gammas[f], (size_t)codes[f]->n * 8);
+    CK(cudaMemcpyAsync(b + o_g, h + o_g, N * 8, cudaMemcpyHostToDevice, s));
+    rc = launch_decode_mixed(ctx, nframes, codes, (const double*)(b + o_g), (double*)(b + o_u),
+                             (uint8_t*)(b + o_h), (int32_t*)(b + o_c), (uint32_t*)(b + o_m),
+                             (lpdec_stats*)(b + o_s), s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h + o_u, b + o_u, tot - o_u, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (size_t f = 0, on = 0, om = 0; f < nf; on += codes[f]->n, om += codes[f]->m, ++f) {
+        const size_t n = codes[f]->n, m = codes[f]->m;
+        std::memcpy(u_out[f], h + o_u + on * 8, n * 8);
+        std::memcpy(hard_out[f], h + o_h + on, n);
+        if (cut_mask_out && cut_mask_out[f]) std::memcpy(cut_mask_out[f], h + o_m + om * 4, m * 4);
+    }
+    std::memcpy(cert_out, h + o_c, nf * 4);
+    if (stats) std::memcpy(stats, h + o_s, nf * sizeof(lpdec_stats));
+    return LPDEC_OK;
+}
+
+int32_t lpdec_decode_mixed_device(lpdec_ctx* ctx, int32_t nframes, const lpdec_code* const* codes,
+                                  const double* d_gamma, double* d_u, uint8_t* d_hard,
+                                  int32_t* d_cert, uint32_t* d_cut_mask, lpdec_stats* d_stats,
+                                  void* stream) {
+    if (!ctx || nframes < 0) return LPDEC_ERR_INVALID_ARG;
+    if (nframes == 0) return LPDEC_OK;
+    if (!codes || !d_gamma || !d_u || !d_hard || !d_cert) return LPDEC_ERR_INVALID_ARG;
+    for (int f = 0; f < nframes; ++f) {
+        int32_t rc = check_ctx_code(ctx, codes[f]);
+        if (rc) return rc;
+    }
+    std::lock_guard<std::mutex> g(ctx->mu);
+    return launch_decode_mixed(ctx, nframes, codes, d_gamma, d_u, d_hard, d_cert, d_cut_mask,
+                               d_stats, (cudaStream_t)stream);
 }
 
 int32_t lpdec_cut_search_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
@@ -715,11 +981,11 @@ int32_t lpdec_cut_search_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t 
     CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
     if (mixed)
         k_cut_search<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-        view_of(code), to_dev(ctx->prm), ln.L, d_u, d_active, d_in_lp, d_mask, d_flag, nframes,
+        view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_u, d_active, d_in_lp, d_mask, d_flag, nframes,
         ctx->counter, ctx->gscratch);
     else
         k_cut_search<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-        view_of(code), to_dev(ctx->prm), ln.L, d_u, d_active, d_in_lp, d_mask, d_flag, nframes,
+        view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_u, d_active, d_in_lp, d_mask, d_flag, nframes,
         ctx->counter, ctx->gscratch);
     CK(cudaGetLastError());
     return LPDEC_OK;
@@ -744,11 +1010,11 @@ int32_t lpdec_mts_select_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t 
     CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
     if (mixed)
         k_mts_select<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_w, d_col, d_row,
+        view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_w, d_col, d_row,
         nframes, ctx->counter, ctx->gscratch);
     else
         k_mts_select<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_w, d_col, d_row,
+        view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_w, d_col, d_row,
         nframes, ctx->counter, ctx->gscratch);
     CK(cudaGetLastError());
     return LPDEC_OK;
@@ -773,11 +1039,11 @@ int32_t lpdec_pcg_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes
     CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
     if (mixed)
         k_pcg<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_dy,
+        view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_dy,
         d_iters, nframes, ctx->counter, ctx->gscratch);
     else
         k_pcg<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_dy,
+        view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_dy,
         d_iters, nframes, ctx->counter, ctx->gscratch);
     CK(cudaGetLastError());
     return LPDEC_OK;
@@ -815,11 +1081,11 @@ int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code, int3
     CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
     if (mixed)
         k_lp_solve<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_x, d_stats, nframes,
+        view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_x, d_stats, nframes,
         ctx->counter, ctx->gscratch, d_trace, d_trace ? max_trace : 0);
     else
         k_lp_solve<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-        view_of(code), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_x, d_stats, nframes,
+        view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_x, d_stats, nframes,
         ctx->counter, ctx->gscratch, d_trace, d_trace ? max_trace : 0);
     CK(cudaGetLastError());
     return LPDEC_OK;
@@ -845,22 +1111,15 @@ constexpr size_t kNoAllocCounterBytes = 256;                 // queue counter sl
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_noalloc_mu;
-constexpr int kMaxDevices = 128;
-char* g_noalloc_base[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on the current device (taken once per
-// device). In host code the symbol is only a host-side stand-in; the kernel
-// must be given the address returned here.
-int32_t noalloc_base(int device, char** out) {
-    if (device < 0 || device >= kMaxDevices) return LPDEC_ERR_NO_DEVICE;
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_base[device]) {
-        void* ptr = nullptr;
-        CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-        g_noalloc_base[device] = static_cast<char*>(ptr);
-    }
-    *out = g_noalloc_base[device];
+// Device address of g_noalloc_scratch in the current device's context. In
+// host code the symbol is only a host-side stand-in; the kernel must be
+// given the address returned here. It is taken on every call (no
+// allocation, and no stale address after a context reset); the first call
+// on a device may load the module.
+int32_t noalloc_base(char** out) {
+    void* ptr = nullptr;
+    CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    *out = static_cast<char*>(ptr);
     return LPDEC_OK;
 }
 
@@ -874,13 +1133,19 @@ int32_t noalloc_launch_plan(const lpdec_params& prm, const lpdec_code* code, int
     threads = std::max(32, std::min(512, threads / 32 * 32));
     size_t cap = (size_t)optin - sizeof(KernelShared) - 1024;
     size_t budget = prm.smem_budget > 0 ? std::min((size_t)prm.smem_budget, cap) : cap;
-    Layout L = make_layout(code->n, code->m, code->E, budget, real_bytes,
-                           prm.precision == LPDEC_M32, false);
+    Dims d;
+    d.cover(view_of(code, prm));
+    const size_t avail = kNoAllocScratchBytes - kNoAllocCounterBytes;
+    // The dense fallback of stalled Newton solves, as in the regular entry,
+    // whenever one CTA's workspace with its matrix fits the array; the grid
+    // then shrinks to the CTAs the array holds.
+    Layout L = make_layout(d, budget, real_bytes, prm.precision == LPDEC_M32, dense_rows_for(d));
+    if (L.smem_bytes != 0xffffffffu && L.gbytes > avail)
+        L = make_layout(d, budget, real_bytes, prm.precision == LPDEC_M32, 0);
     if (L.smem_bytes == 0xffffffffu || L.smem_bytes + sizeof(KernelShared) > (size_t)optin) {
         snprintf(g_err, sizeof g_err, "frame workspace does not fit in shared memory");
         return LPDEC_ERR_INVALID_ARG;
     }
-    const size_t avail = kNoAllocScratchBytes - kNoAllocCounterBytes;
     if (L.gbytes > avail) {
         snprintf(g_err, sizeof g_err,
                  "one frame needs %llu bytes of scratch, above the %zu-byte static array",
@@ -915,14 +1180,12 @@ extern "C" int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
         return LPDEC_ERR_INVALID_ARG;
     lpdec_params prm;
     if (params) prm = *params; else lpdec_default_params(&prm);
-    if (prm.variant != LPDEC_MALP_A && prm.variant != LPDEC_MALP_B) return LPDEC_ERR_INVALID_ARG;
-    if (prm.precision != LPDEC_FP64 && prm.precision != LPDEC_MIXED && prm.precision != LPDEC_M32)
-        return LPDEC_ERR_INVALID_ARG;
+    if (!params_ok(prm)) return LPDEC_ERR_INVALID_ARG;
     if (nframes == 0) return LPDEC_OK;
-    const int device = code->ctx->device;
+    const int device = code->device;
     CK(cudaSetDevice(device));
     char* base = nullptr;
-    int32_t rc = noalloc_base(device, &base);
+    int32_t rc = noalloc_base(&base);
     if (rc) return rc;
     const bool mixed = prm.precision == LPDEC_MIXED;
     Launch ln;
@@ -935,11 +1198,13 @@ extern "C" int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
     CK(cudaMemsetAsync(counter, 0, sizeof(int), s));   // the only state a call must reset
     if (mixed)
         k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            view_of(code), to_dev(prm), ln.L, d_gamma, d_u, d_hard, d_cert, d_cut_mask, d_stats,
+            view_of(code, prm), nullptr, nullptr, to_dev(prm), ln.L, d_gamma, d_u, d_hard,
+            d_cert, d_cut_mask, d_stats,
             nframes, counter, gscratch);
     else
         k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            view_of(code), to_dev(prm), ln.L, d_gamma, d_u, d_hard, d_cert, d_cut_mask, d_stats,
+            view_of(code, prm), nullptr, nullptr, to_dev(prm), ln.L, d_gamma, d_u, d_hard,
+            d_cert, d_cut_mask, d_stats,
             nframes, counter, gscratch);
     CK(cudaGetLastError());
     return LPDEC_OK;

@@ -17,18 +17,21 @@
 namespace lpdec {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint8_t kInLP = 1;     // check j has a parity inequality in the LP
-constexpr uint8_t kActive = 2;   // ... and it is active at the last LP solution
+constexpr uint8_t kInLP = 1;     // check j has at least one parity inequality in the LP
+constexpr uint8_t kActive = 2;   // ... and one of them is active at the last LP solution
+constexpr uint8_t kNew = 4;      // the cut search found a violated inequality of j this round
 constexpr uint16_t kNone = 0xffffu;
 constexpr uint16_t kNeg = 0x8000u;   // packed entry: index | kNeg if the coefficient is -1
 constexpr uint16_t kIdx = 0x7fffu;
 
 // ---------------------------------------------------------------------------
 // Code (H) view: CSR rows = checks, CSC columns = bits. Read-only, shared by
-// every frame of a batch (n, m <= 32767).
+// every frame of the code (n, m <= 32767). pmax / eamax: capacity of one
+// frame's LP (rows, and nonzeros of the standard part of A).
 // ---------------------------------------------------------------------------
 struct CodeView {
     int n, m, E;
+    int pmax, eamax;
     const int* __restrict__ h_ptr;   // [m+1]
     const int* __restrict__ h_col;   // [E] bit of CSR edge e
     const int* __restrict__ e_chk;   // [E] check of CSR edge e
@@ -44,21 +47,25 @@ struct DevParams {
 };
 
 // ---------------------------------------------------------------------------
-// Workspace layout (the host decides shared vs global placement)
+// Workspace layout (the host decides shared vs global placement). Arrays over
+// LP rows have the capacity pmax, arrays over columns n + pmax.
 // ---------------------------------------------------------------------------
 enum Arr {
-    // hot arrays (shared memory)
-    S_ROWENT, S_COLENT, S_ROWCHK, S_CHKROW, S_PIVCOL, S_PIVROW, S_PSGN,
+    // LP structure: cut list (rows grouped by check), packed row entries and
+    // column entries of A, per-check row pointers
+    S_ROWENT, S_COLENT, S_CCHK, S_CMASK, S_CACT, S_RPTR, S_CPTR, S_CRPTR,
+    // preconditioner selection and the two level-scheduled triangular solves
+    S_PIVCOL, S_PIVROW, S_PSGN,
     S_LB, S_LF, S_LBPTR, S_LFPTR, S_CUR, S_LBROWS, S_LFROWS, S_SELROW,
     S_DEG, S_BITMAP, S_FLAGS, S_MASK, S_FLIP, S_HPTR, S_VPTR,
     S_BPTR, S_BDEP, S_FPTR, S_FDEP,   // dependency lists of the two triangular solves
-    S_VEC,      // PCG vectors of type T: xs, r, z, h, l (m each), t (n), d2t (n+m), invd2p (m);
-                // during the MTS selection the same bytes hold the u64 sort keys
-                // [q2] followed by rank [q] and sorted [q] (uint16)
+    S_VEC,      // PCG vectors of type T: xs, r, z, h, l (pmax each), t (n), d2t (n+pmax),
+                // invd2p (pmax); during the MTS selection the same bytes hold the u64
+                // sort keys [q2] followed by rank [q] and sorted [q] (uint16)
     // FP64 interior-point state (global scratch)
     G_X, G_Z, G_RC, G_D2, G_Y, G_B, G_W, G_DY, G_R64, G_U, G_T64, G_BASIC,
     // optimality certificate scratch: vertex and CG vectors over columns
-    // (4 x n+m) and rows (2 x m)
+    // (4 x n+pmax) and rows (2 x pmax)
     G_VX, G_V1, G_V2, G_V3, G_V4, G_VR1, G_VR2,
     // FP64 PCG vectors for the fallback rounds of the mixed mode (layout of
     // S_VEC with T = double)
@@ -66,46 +73,54 @@ enum Arr {
     // dense p x p FP64 matrix of the Cholesky fallback of the Newton solve
     // (16 bytes when the fallback is off)
     G_QD,
+    // cut list being rebuilt (rows, masks, per-check row pointers) after a cut search
+    G_CCHK2, G_CMASK2, G_CRPTR2,
     A_COUNT
 };
 
 constexpr uint32_t kGlobalBit = 0x80000000u;
 
-// Elements of type T in the S_VEC block: xs, r, z, h, l (m each), t (n),
-// d2t (n + m), invd2p (m).
-__host__ __device__ constexpr size_t vec_elems(int n, int m) {
-    return 7 * (size_t)m + 2 * (size_t)n;
+// Elements of type T in the S_VEC block: xs, r, z, h, l (pmax each), t (n),
+// d2t (n + pmax), invd2p (pmax).
+__host__ __device__ constexpr size_t vec_elems(int n, int pmax) {
+    return 7 * (size_t)pmax + 2 * (size_t)n;
 }
 // Bytes of the S_VEC block: the vectors above in type T and, for
 // LPDEC_M32, three FP32 vectors after them (the M-solve's right side and
 // solution, and 1/d^2 of the pivot columns).
-__host__ __device__ constexpr size_t vec_bytes(int n, int m, size_t real_bytes, bool m32) {
-    return real_bytes * vec_elems(n, m) + (m32 ? 12 * (size_t)m : 0);
+__host__ __device__ constexpr size_t vec_bytes(int n, int pmax, size_t real_bytes, bool m32) {
+    return real_bytes * vec_elems(n, pmax) + (m32 ? 12 * (size_t)pmax : 0);
 }
 
 struct Layout {
     uint32_t off[A_COUNT];     // byte offset; kGlobalBit set = global scratch
     uint32_t smem_bytes;       // dynamic shared memory per CTA
-    uint32_t q2;               // power of two >= n + m (sort width)
-    uint32_t dense;            // 1 = G_QD holds an m x m FP64 matrix
+    uint32_t q2;               // power of two >= nmax + pmax (sort width)
+    uint32_t dense;            // 1 = G_QD holds a pmax x pmax FP64 matrix
+    uint32_t nmax, mmax, pmax; // capacities the arrays are sized for
     unsigned long long gbytes; // global scratch bytes per CTA
 };
 
 template <typename T>
 struct WS {
-    uint16_t *rowent, *colent, *rowchk, *chkrow, *pivcol, *pivrow, *lb, *lf, *lbrows, *lfrows;
-    uint16_t *selrow, *rank, *sorted;
+    uint16_t *rowent, *colent, *cchk, *pivcol, *pivrow, *lb, *lf, *lbrows, *lfrows;
+    uint16_t *selrow, *rank, *sorted, *deg;
+    uint32_t *cmask, *rptr, *cptr, *crptr;
     uint32_t *lbptr, *lfptr, *cur, *bitmap, *mask, *flip;
     int *hptr, *vptr;   // shared copies of the code's CSR / CSC row pointers
     uint32_t *bptr, *fptr;
     uint16_t *bdep, *fdep;   // packed (row | kNeg): rows whose solved values row r needs
-    uint8_t *psgn, *deg, *flags, *basic;
+    uint8_t *cact, *psgn, *flags, *basic;
     T *xs, *r, *z, *h, *l, *t, *d2t, *invd2p;
     float *rf, *zf, *ip32;      // FP32 M-solve vectors (LPDEC_M32 only)
     unsigned long long* skey;   // aliases the PCG vectors
     double *x, *zz, *rc, *d2, *y, *b, *w, *dy, *r64, *u, *t64;
     double *vx, *v1, *v2, *v3, *v4, *vr1, *vr2, *p64;
     double* qd;   // dense Cholesky factor (column-major p x p), null when off
+    uint16_t* cchk2;
+    uint32_t *cmask2, *crptr2;
+    int cap_n, cap_p;   // capacities the sub-arrays were sliced with
+    int dense_p;        // rows the dense fallback's matrix holds (0: off)
 };
 
 __device__ __forceinline__ char* ws_ptr(const Layout& L, int a, char* smem, char* gws) {
@@ -113,18 +128,22 @@ __device__ __forceinline__ char* ws_ptr(const Layout& L, int a, char* smem, char
     return (o & kGlobalBit) ? gws + (o & ~kGlobalBit) : smem + o;
 }
 
+// Pointers of one CTA's workspace; sub-arrays of S_VEC and G_P64 are sliced
+// with the layout's capacities, so frames of any smaller code fit.
 template <typename T>
-__device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws, int n, int m, int q2) {
+__device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws) {
+    const int n = (int)L.nmax, pm = (int)L.pmax;
     WS<T> w;
 #define P_(Ty, name, id) w.name = reinterpret_cast<Ty*>(ws_ptr(L, id, smem, gws))
     P_(uint16_t, rowent, S_ROWENT); P_(uint16_t, colent, S_COLENT);
-    P_(uint16_t, rowchk, S_ROWCHK); P_(uint16_t, chkrow, S_CHKROW);
+    P_(uint16_t, cchk, S_CCHK); P_(uint32_t, cmask, S_CMASK); P_(uint8_t, cact, S_CACT);
+    P_(uint32_t, rptr, S_RPTR); P_(uint32_t, cptr, S_CPTR); P_(uint32_t, crptr, S_CRPTR);
     P_(uint16_t, pivcol, S_PIVCOL); P_(uint16_t, pivrow, S_PIVROW);
     P_(uint8_t, psgn, S_PSGN);
     P_(uint16_t, lb, S_LB); P_(uint16_t, lf, S_LF);
     P_(uint32_t, lbptr, S_LBPTR); P_(uint32_t, lfptr, S_LFPTR); P_(uint32_t, cur, S_CUR);
     P_(uint16_t, lbrows, S_LBROWS); P_(uint16_t, lfrows, S_LFROWS); P_(uint16_t, selrow, S_SELROW);
-    P_(uint8_t, deg, S_DEG);
+    P_(uint16_t, deg, S_DEG);
     P_(uint32_t, bitmap, S_BITMAP); P_(uint8_t, flags, S_FLAGS); P_(uint32_t, mask, S_MASK);
     P_(uint32_t, flip, S_FLIP);
     P_(int, hptr, S_HPTR); P_(int, vptr, S_VPTR);
@@ -132,11 +151,11 @@ __device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws, int n, i
     P_(uint16_t, bdep, S_BDEP); P_(uint16_t, fdep, S_FDEP);
     T* v = reinterpret_cast<T*>(ws_ptr(L, S_VEC, smem, gws));
     w.skey = reinterpret_cast<unsigned long long*>(v);
-    w.rank = reinterpret_cast<uint16_t*>(w.skey + q2);
-    w.sorted = w.rank + (n + m);
-    w.xs = v; v += m; w.r = v; v += m; w.z = v; v += m; w.h = v; v += m; w.l = v; v += m;
-    w.t = v; v += n; w.d2t = v; v += n + m; w.invd2p = v;
-    w.rf = reinterpret_cast<float*>(w.invd2p + m); w.zf = w.rf + m; w.ip32 = w.zf + m;
+    w.rank = reinterpret_cast<uint16_t*>(w.skey + L.q2);
+    w.sorted = w.rank + (n + pm);
+    w.xs = v; v += pm; w.r = v; v += pm; w.z = v; v += pm; w.h = v; v += pm; w.l = v; v += pm;
+    w.t = v; v += n; w.d2t = v; v += n + pm; w.invd2p = v;
+    w.rf = reinterpret_cast<float*>(w.invd2p + pm); w.zf = w.rf + pm; w.ip32 = w.zf + pm;
     P_(double, x, G_X); P_(double, zz, G_Z); P_(double, rc, G_RC); P_(double, d2, G_D2);
     P_(double, y, G_Y); P_(double, b, G_B); P_(double, w, G_W); P_(double, dy, G_DY);
     P_(double, r64, G_R64); P_(double, u, G_U); P_(double, t64, G_T64);
@@ -145,7 +164,12 @@ __device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws, int n, i
     P_(double, v4, G_V4); P_(double, vr1, G_VR1); P_(double, vr2, G_VR2);
     P_(double, p64, G_P64);
     P_(double, qd, G_QD);
+    P_(uint16_t, cchk2, G_CCHK2); P_(uint32_t, cmask2, G_CMASK2);
+    P_(uint32_t, crptr2, G_CRPTR2);
     if (!L.dense) w.qd = nullptr;
+    w.dense_p = (int)L.dense;
+    w.cap_n = n;
+    w.cap_p = pm;
 #undef P_
     return w;
 }
@@ -154,9 +178,14 @@ __device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws, int n, i
 // structure, for the FP64 fallback rounds of the mixed mode. d2t is the FP64
 // D^2 itself.
 template <typename T>
-__device__ inline WS<double> fp64_view(const WS<T>& W, int n, int m) {
+__device__ inline WS<double> fp64_view(const WS<T>& W) {
+    const int n = W.cap_n, pm = W.cap_p;
     WS<double> v;
-    v.rowent = W.rowent; v.colent = W.colent; v.rowchk = W.rowchk; v.chkrow = W.chkrow;
+    v.cap_n = n;
+    v.cap_p = pm;
+    v.dense_p = W.dense_p;
+    v.rowent = W.rowent; v.colent = W.colent; v.cchk = W.cchk; v.cmask = W.cmask;
+    v.cact = W.cact; v.rptr = W.rptr; v.cptr = W.cptr; v.crptr = W.crptr;
     v.pivcol = W.pivcol; v.pivrow = W.pivrow; v.lb = W.lb; v.lf = W.lf; v.lbrows = W.lbrows;
     v.lfrows = W.lfrows; v.selrow = W.selrow; v.rank = W.rank; v.sorted = W.sorted;
     v.lbptr = W.lbptr; v.lfptr = W.lfptr; v.cur = W.cur; v.bitmap = W.bitmap; v.mask = W.mask;
@@ -164,7 +193,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W, int n, int m) {
     v.hptr = W.hptr; v.vptr = W.vptr;
     v.bptr = W.bptr; v.fptr = W.fptr; v.bdep = W.bdep; v.fdep = W.fdep;
     double* q = W.p64;
-    v.xs = q; q += m; v.r = q; q += m; v.z = q; q += m; v.h = q; q += m; v.l = q; q += m;
+    v.xs = q; q += pm; v.r = q; q += pm; v.z = q; q += pm; v.h = q; q += pm; v.l = q; q += pm;
     v.t = q; q += n; v.invd2p = q;
     v.rf = W.rf; v.zf = W.zf; v.ip32 = W.ip32;
     v.d2t = W.d2;
@@ -173,6 +202,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W, int n, int m) {
     v.dy = W.dy; v.r64 = W.r64; v.u = W.u; v.t64 = W.t64;
     v.vx = W.vx; v.v1 = W.v1; v.v2 = W.v2; v.v3 = W.v3; v.v4 = W.v4; v.vr1 = W.vr1;
     v.vr2 = W.vr2; v.p64 = W.p64; v.qd = W.qd;
+    v.cchk2 = W.cchk2; v.cmask2 = W.cmask2; v.crptr2 = W.crptr2;
     return v;
 }
 
@@ -180,6 +210,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W, int n, int m) {
 // memory) and returns a view of the code that reads them from there.
 template <typename T>
 __device__ inline CodeView bind_code(const CodeView& C, WS<T>& W) {
+    __syncthreads();   // the previous frame may still read the old pointers
     for (int k = threadIdx.x; k <= C.m; k += blockDim.x) W.hptr[k] = C.h_ptr[k];
     for (int k = threadIdx.x; k <= C.n; k += blockDim.x) W.vptr[k] = C.v_ptr[k];
     __syncthreads();
@@ -281,7 +312,7 @@ struct Frame {
     int ea;         // nonzeros of the standard part of A (sum of the LP rows' degrees)
 };
 
-// u^0 = bitwise hard decision (Eq. 8); empty cut set.
+// u^0 = bitwise hard decision (Eq. 8); empty cut list.
 template <typename T>
 __device__ inline void frame_init(Blk& B, const CodeView& C, WS<T>& W, const double* gamma) {
     for (int i = B.tid; i < C.n; i += B.nt) W.u[i] = gamma[i] < 0.0 ? 1.0 : 0.0;
@@ -294,19 +325,23 @@ __device__ inline void frame_init(Blk& B, const CodeView& C, WS<T>& W, const dou
         W.flip[k] = bits;
     }
     for (int j = B.tid; j < C.m; j += B.nt) { W.flags[j] = 0; W.mask[j] = 0; }
+    for (int j = B.tid; j <= C.m; j += B.nt) W.crptr[j] = 0;
     __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-// a1: cut search — Algorithm 2 per check inside the loop of Algorithm 3.
-// One warp per check, lanes = neighbours (d_j <= 32).
+// a1: cut search — Algorithm 2 per check inside the loop of Algorithm 3 (or
+// Algorithm 1). One warp per check, lanes = neighbours (d_j <= 32). MALP
+// searches the checks without an active inequality; ALP searches every
+// check. A violated check gets kNew and its set V in mask[j].
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ inline int cut_search(Blk& B, const CodeView& C, WS<T>& W, const DevParams& P) {
+__device__ inline int cut_search(Blk& B, const CodeView& C, WS<T>& W, const DevParams& P,
+                                 bool alp) {
     int added = 0;
     for (int j = B.warp; j < C.m; j += B.nwarps) {
         uint8_t f = W.flags[j];
-        if ((f & kInLP) && (f & kActive)) continue;   // j has an active inequality
+        if (!alp && (f & kInLP) && (f & kActive)) continue;   // j has an active inequality
         int beg = C.h_ptr[j];
         int d = C.h_ptr[j + 1] - beg;
         if (d <= 0) continue;
@@ -323,7 +358,7 @@ __device__ inline int cut_search(Blk& B, const CodeView& C, WS<T>& W, const DevP
         double term = valid ? (((V >> B.lane) & 1u) ? 1.0 - ui : ui) : 0.0;
         double lhs = warp_sum(term);                               // left side of Eq. 6
         if (lhs < 1.0 - P.tau_cut) {
-            if (B.lane == 0) { W.mask[j] = V; W.flags[j] = kInLP; }
+            if (B.lane == 0) { W.mask[j] = V; W.flags[j] = f | kInLP | kNew; }
             added = 1;
         }
     }
@@ -341,73 +376,136 @@ __device__ inline void drop_inactive(Blk& B, const CodeView& C, WS<T>& W) {
 }
 
 // ---------------------------------------------------------------------------
-// a2: augmented LP (Eq. 16) from the cut set. Coefficients are +-1:
-// a_{r,i} = s_i (unflipped) or -s_i (flipped), s_i = +1 iff i in V, and
-// b_r = |V| - 1 - sum_{flipped i in N(j)} s_i. The LP's pattern is packed
-// per CSR edge (rowent: bit | sign) and per CSC entry (colent: LP row |
-// sign, or kNone when the check is not in the LP).
+// a2: augmented LP (Eq. 16) from the cut list. A row r is a cut (check
+// cchk[r], odd set cmask[r]); rows are grouped by check (crptr[j] .. crptr[j+1])
+// and ordered by insertion inside a check. Rebuilding the list after a cut
+// search keeps a check's old rows unless it is not in the LP any more or
+// (MALP, alp = false) its new cut replaces them, and appends the new cut.
+// Coefficients are +-1: a_{r,i} = s_i (unflipped) or -s_i (flipped),
+// s_i = +1 iff i in V, and b_r = |V| - 1 - sum_{flipped i in N(j)} s_i.
+// Packed entries: rowent[rptr[r] + t] = bit | sign of the t-th neighbour of
+// the row's check; colent[cptr[i] ..] = (row | sign) over the rows that hold
+// bit i, in increasing row order. Returns false (LP left unchanged) when the
+// new list exceeds the frame's capacity (C.pmax rows, C.eamax entries).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ inline void lp_build(Blk& B, const CodeView& C, WS<T>& W, Frame& F, int* shscan) {
+__device__ inline bool lp_build(Blk& B, const CodeView& C, WS<T>& W, Frame& F, int* shscan,
+                                bool alp) {
+    // 1. new cut list, grouped by check
     int per = (C.m + B.nt - 1) / B.nt;
     int j0 = B.tid * per, j1 = min(C.m, j0 + per);
-    int cnt = 0;
-    for (int j = j0; j < j1; ++j) cnt += (W.flags[j] & kInLP) ? 1 : 0;
-    int total;
-    int pos = bscan_excl(B, cnt, &total, shscan);
+    int cnt = 0, cne = 0;
     for (int j = j0; j < j1; ++j) {
-        if (W.flags[j] & kInLP) { W.rowchk[pos] = (uint16_t)j; W.chkrow[j] = (uint16_t)pos; ++pos; }
-        else W.chkrow[j] = kNone;
+        uint8_t f = W.flags[j];
+        int kept = ((f & kInLP) && !(!alp && (f & kNew))) ? (int)(W.crptr[j + 1] - W.crptr[j]) : 0;
+        int c = kept + ((f & kNew) ? 1 : 0);
+        cnt += c;
+        cne += c * (C.h_ptr[j + 1] - C.h_ptr[j]);
     }
-    F.p = total;
-    F.q = C.n + total;
-    for (int e = B.tid; e < C.E; e += B.nt) {
-        int j = C.e_chk[e];
-        int i = C.h_col[e];
-        bool inV = (W.mask[j] >> (e - C.h_ptr[j])) & 1u;
-        bool neg = inV == flipped(W.flip, i);
-        W.rowent[e] = (uint16_t)(i | (neg ? kNeg : 0));
+    int p, ne_all;
+    int pos = bscan_excl(B, cnt, &p, shscan);
+    bscan_excl(B, cne, &ne_all, shscan);
+    if (p > C.pmax || ne_all > C.eamax) return false;   // same decision in every thread
+    // (the old list is only read until the barrier; the new one goes to the
+    // G_*2 arrays first)
+    for (int j = j0; j < j1; ++j) {
+        uint8_t f = W.flags[j];
+        W.crptr2[j] = (uint32_t)pos;
+        if ((f & kInLP) && !(!alp && (f & kNew)))
+            for (uint32_t r = W.crptr[j]; r < W.crptr[j + 1]; ++r) {
+                W.cchk2[pos] = (uint16_t)j;
+                W.cmask2[pos] = W.cmask[r];
+                ++pos;
+            }
+        if (f & kNew) { W.cchk2[pos] = (uint16_t)j; W.cmask2[pos] = W.mask[j]; ++pos; }
     }
+    if (B.tid == 0) W.crptr2[C.m] = (uint32_t)p;
     __syncthreads();
-    for (int k = B.tid; k < C.E; k += B.nt) {
-        uint16_t r = W.chkrow[C.v_chk[k]];
-        W.colent[k] = (r == kNone) ? kNone : (uint16_t)(r | (W.rowent[C.v_eidx[k]] & kNeg));
+    for (int j = B.tid; j <= C.m; j += B.nt) {
+        const uint32_t a = W.crptr2[j];
+        W.crptr[j] = a;
+        // kNew consumed; activity is set by the next LP
+        if (j < C.m) W.flags[j] = (W.crptr2[j + 1] > a) ? kInLP : 0;
     }
-    double nb2 = 0.0, ea = 0.0;
-    for (int r = B.tid; r < F.p; r += B.nt) {
-        int j = W.rowchk[r];
-        ea += C.h_ptr[j + 1] - C.h_ptr[j];
-        uint32_t V = W.mask[j];
+    for (int r = B.tid; r < p; r += B.nt) { W.cchk[r] = W.cchk2[r]; W.cmask[r] = W.cmask2[r]; }
+    __syncthreads();
+    // 2. row pointers (row r holds d_j entries)
+    per = (p + B.nt - 1) / B.nt;
+    const int r0 = B.tid * per, r1 = min(p, r0 + per);
+    int ne = 0;
+    for (int r = r0; r < r1; ++r) { int j = W.cchk[r]; ne += C.h_ptr[j + 1] - C.h_ptr[j]; }
+    int ea;
+    int epos = bscan_excl(B, ne, &ea, shscan);
+    for (int r = r0; r < r1; ++r) {
+        W.rptr[r] = (uint32_t)epos;
+        int j = W.cchk[r];
+        epos += C.h_ptr[j + 1] - C.h_ptr[j];
+    }
+    if (B.tid == 0) W.rptr[p] = (uint32_t)ea;
+    __syncthreads();
+    // 3. row entries and b
+    double nb2 = 0.0;
+    for (int r = B.tid; r < p; r += B.nt) {
+        const int j = W.cchk[r], beg = C.h_ptr[j], d = C.h_ptr[j + 1] - beg;
+        const uint32_t V = W.cmask[r];
+        const uint32_t o = W.rptr[r];
         double shift = 0.0;
-        for (int e = C.h_ptr[j]; e < C.h_ptr[j + 1]; ++e)
-            if (flipped(W.flip, C.h_col[e])) shift += ((V >> (e - C.h_ptr[j])) & 1u) ? 1.0 : -1.0;
+        for (int t = 0; t < d; ++t) {
+            const int i = C.h_col[beg + t];
+            const bool inV = (V >> t) & 1u;
+            const bool fl = flipped(W.flip, i);
+            W.rowent[o + t] = (uint16_t)(i | ((inV == fl) ? kNeg : 0));
+            if (fl) shift += inV ? 1.0 : -1.0;
+        }
         double bv = (double)__popc(V) - 1.0 - shift;
         W.b[r] = bv;
         nb2 += bv * bv;
     }
-    double2 t = bsum2(B, nb2, ea);   // (barrier inside)
-    F.normb = sqrt(t.x);
-    F.ea = (int)t.y;
+    // 4. column pointers and entries (rows of bit i: the rows of its checks)
+    per = (C.n + B.nt - 1) / B.nt;
+    const int i0 = B.tid * per, i1 = min(C.n, i0 + per);
+    int nc = 0;
+    for (int i = i0; i < i1; ++i)
+        for (int k = C.v_ptr[i]; k < C.v_ptr[i + 1]; ++k) {
+            int j = C.v_chk[k];
+            nc += (int)(W.crptr[j + 1] - W.crptr[j]);
+        }
+    int tot;
+    int cpos = bscan_excl(B, nc, &tot, shscan);   // barrier inside: rowent complete
+    for (int i = i0; i < i1; ++i) {
+        W.cptr[i] = (uint32_t)cpos;
+        for (int k = C.v_ptr[i]; k < C.v_ptr[i + 1]; ++k) {
+            const int j = C.v_chk[k];
+            const int t = C.v_eidx[k] - C.h_ptr[j];
+            for (uint32_t r = W.crptr[j]; r < W.crptr[j + 1]; ++r)
+                W.colent[cpos++] = (uint16_t)(r | (W.rowent[W.rptr[r] + t] & kNeg));
+        }
+    }
+    if (B.tid == 0) W.cptr[C.n] = (uint32_t)tot;
+    F.p = p;
+    F.q = C.n + p;
+    F.ea = ea;
+    F.normb = sqrt(bsum(B, nb2));   // (barrier inside)
+    return true;
 }
 
 // (A' v)_i for a standard column i (its LP rows, through colent).
 template <typename V, typename T>
 __device__ __forceinline__ V colA_T(const CodeView& C, const WS<T>& W, int i, const V* v) {
     V acc = V(0);
-    const int k1 = C.v_ptr[i + 1];
-    for (int k = C.v_ptr[i]; k < k1; ++k) {
+    const uint32_t k1 = W.cptr[i + 1];
+    for (uint32_t k = W.cptr[i]; k < k1; ++k) {
         uint16_t ent = W.colent[k];
-        if (ent != kNone) acc += signed_val<V>(ent, v[ent & kIdx]);
+        acc += signed_val<V>(ent, v[ent & kIdx]);
     }
     return acc;
 }
 // (A v)_r over the standard part of LP row r (slack added by the caller).
 template <typename V, typename T>
 __device__ __forceinline__ V rowA(const CodeView& C, const WS<T>& W, int r, const V* vq) {
-    int j = W.rowchk[r];
     V acc = V(0);
-    const int e1 = C.h_ptr[j + 1];
-    for (int e = C.h_ptr[j]; e < e1; ++e) {
+    const uint32_t e1 = W.rptr[r + 1];
+    for (uint32_t e = W.rptr[r]; e < e1; ++e) {
         uint16_t ent = W.rowent[e];
         acc += signed_val<V>(ent, vq[ent & kIdx]);
     }
@@ -418,7 +516,7 @@ __device__ __forceinline__ V rowA(const CodeView& C, const WS<T>& W, int r, cons
 // a4: column-wise greedy MTS (Algorithm 7) with weights wt[0..q).
 // Columns are ranked once by (weight desc, index asc) with a bitonic sort on
 // the weights rounded to FP32; DEG1 is a bitmap over ranks, so "maximum-
-// weight degree-1 column" is the first set bit. Warp 0 runs the p greedy
+// weight degree-1 column" is the first set bit. One warp runs the p greedy
 // steps: lanes scan the bitmap and update the columns of the removed row.
 // The forward-solve level of each row is fixed when its pivot is chosen and
 // the back-substitution levels follow in reverse selection order.
@@ -459,25 +557,21 @@ __device__ inline void build_deps(Blk& B, const CodeView& C, WS<T>& W, const Fra
     const int r0 = B.tid * per, r1 = min(p, r0 + per);
     int cb = 0, cf = 0;
     for (int r = r0; r < r1; ++r) {
-        const int i0 = W.pivcol[r], j = W.rowchk[r];
-        for (int e = C.h_ptr[j]; e < C.h_ptr[j + 1]; ++e) {
+        const int i0 = W.pivcol[r];
+        for (uint32_t e = W.rptr[r]; e < W.rptr[r + 1]; ++e) {
             int i2 = W.rowent[e] & kIdx;
             cb += (i2 != i0 && W.pivrow[i2] != kNone);
         }
-        if (i0 < n)
-            for (int k = C.v_ptr[i0]; k < C.v_ptr[i0 + 1]; ++k) {
-                uint16_t ent = W.colent[k];
-                cf += (ent != kNone && (ent & kIdx) != r);
-            }
+        if (i0 < n) cf += (int)(W.cptr[i0 + 1] - W.cptr[i0]) - 1;
     }
     int tb, tf;
     int ob = bscan_excl(B, cb, &tb, sh);
     int of = bscan_excl(B, cf, &tf, sh);
     for (int r = r0; r < r1; ++r) {
-        const int i0 = W.pivcol[r], j = W.rowchk[r];
+        const int i0 = W.pivcol[r];
         W.bptr[r] = ob;
         W.fptr[r] = of;
-        for (int e = C.h_ptr[j]; e < C.h_ptr[j + 1]; ++e) {
+        for (uint32_t e = W.rptr[r]; e < W.rptr[r + 1]; ++e) {
             uint16_t ent = W.rowent[e];
             int i2 = ent & kIdx;
             if (i2 == i0) continue;
@@ -485,122 +579,20 @@ __device__ inline void build_deps(Blk& B, const CodeView& C, WS<T>& W, const Fra
             if (pr != kNone) W.bdep[ob++] = (uint16_t)(pr | (ent & kNeg));
         }
         if (i0 < n)
-            for (int k = C.v_ptr[i0]; k < C.v_ptr[i0 + 1]; ++k) {
+            for (uint32_t k = W.cptr[i0]; k < W.cptr[i0 + 1]; ++k) {
                 uint16_t ent = W.colent[k];
-                if (ent != kNone && (ent & kIdx) != r) W.fdep[of++] = ent;
+                if ((ent & kIdx) != r) W.fdep[of++] = ent;
             }
     }
     if (B.tid == 0) { W.bptr[p] = tb; W.fptr[p] = tf; }
     __syncthreads();
 }
 
+// Level buckets (counting sort) of both solves from lb / lf, pivot signs,
+// and the dependency lists. Shared by every MTS selection.
 template <typename T>
-__device__ inline Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
-                                    const double* wt, int q2) {
-    const int n = C.n, p = F.p, q = F.q;
-    for (int i = B.tid; i < q; i += B.nt) {
-        int dg = 1;
-        if (i < n) {
-            dg = 0;
-            for (int k = C.v_ptr[i]; k < C.v_ptr[i + 1]; ++k) dg += (W.colent[k] != kNone);
-        }
-        W.deg[i] = (uint8_t)dg;
-        W.pivrow[i] = kNone;
-    }
-    for (int k = B.tid; k < q2; k += B.nt)
-        W.skey[k] = (k < q) ? (((unsigned long long)desc_key32((float)wt[k]) << 32) | (unsigned)k)
-                            : ~0ull;
-    for (int r = B.tid; r < p; r += B.nt) { W.pivcol[r] = kNone; W.lb[r] = 1; W.lf[r] = 1; }
-    __syncthreads();
-    bitonic_sort(B, W.skey, q2);
-    const int nw = (q + 31) / 32;
-    for (int k = B.tid; k < nw; k += B.nt) W.bitmap[k] = 0;
-    for (int k = B.tid; k < q; k += B.nt) {
-        int i = (int)(W.skey[k] & 0xffffffffu);
-        W.rank[i] = (uint16_t)k;
-        W.sorted[k] = (uint16_t)i;
-    }
-    __syncthreads();
-    for (int i = B.tid; i < q; i += B.nt)
-        if (W.deg[i] == 1) atomicOr(&W.bitmap[W.rank[i] >> 5], 1u << (W.rank[i] & 31));
-    __syncthreads();
-
-    if (B.warp == B.sw) {
-        const int lane = B.lane;
-        for (int k = 0; k < p; ++k) {
-            unsigned best = 0xffffffffu;
-            for (int wd = lane; wd < nw; wd += 32) {
-                uint32_t v = W.bitmap[wd];
-                if (v) { best = (unsigned)(wd * 32 + __ffs(v) - 1); break; }
-            }
-            best = __reduce_min_sync(kFull, best);
-            if (best >= (unsigned)q) break;   // cannot happen: every live row keeps its slack
-            int i = W.sorted[best];
-            int jr, lev;
-            if (i >= n) {
-                jr = i - n;
-                lev = 1;
-            } else {
-                int beg = C.v_ptr[i], d = C.v_ptr[i + 1] - beg;
-                unsigned cand = 0xffffffffu;
-                int lv = 0;
-                for (int t = lane; t < d; t += 32) {
-                    uint16_t ent = W.colent[beg + t];
-                    if (ent != kNone) {
-                        int r = ent & kIdx;
-                        if (W.pivcol[r] == kNone) cand = min(cand, (unsigned)r);
-                        else lv = max(lv, (int)W.lf[r]);
-                    }
-                }
-                unsigned jm = __reduce_min_sync(kFull, cand);
-                lev = (int)__reduce_max_sync(kFull, (unsigned)lv) + 1;
-                if (jm >= (unsigned)p) break;  // cannot happen: i has degree one
-                jr = (int)jm;
-            }
-            __syncwarp();
-            if (lane == 0) {
-                W.pivcol[jr] = (uint16_t)i;
-                W.pivrow[i] = (uint16_t)jr;
-                W.lf[jr] = (uint16_t)lev;
-                W.selrow[k] = (uint16_t)jr;
-                atomicAnd(&W.bitmap[best >> 5], ~(1u << (best & 31)));
-            }
-            __syncwarp();
-            // zero row jr: every other live column of the row loses one degree
-            int j = W.rowchk[jr];
-            int beg = C.h_ptr[j], d = C.h_ptr[j + 1] - beg;
-            for (int t = lane; t <= d; t += 32) {
-                int i2 = (t < d) ? (W.rowent[beg + t] & kIdx) : n + jr;
-                if (W.pivrow[i2] != kNone) continue;   // taken (includes i)
-                int nd = (int)W.deg[i2] - 1;
-                W.deg[i2] = (uint8_t)nd;
-                int rk = W.rank[i2];
-                if (nd == 1) atomicOr(&W.bitmap[rk >> 5], 1u << (rk & 31));
-                else if (nd == 0) atomicAnd(&W.bitmap[rk >> 5], ~(1u << (rk & 31)));
-            }
-            __syncwarp();
-        }
-        // back-substitution levels, in reverse selection order
-        for (int k = p - 1; k >= 0; --k) {
-            int r = W.selrow[k];
-            int i0 = W.pivcol[r];
-            int j = W.rowchk[r];
-            int beg = C.h_ptr[j], d = C.h_ptr[j + 1] - beg;
-            int lv = 0;
-            for (int t = lane; t < d; t += 32) {
-                int i2 = W.rowent[beg + t] & kIdx;
-                if (i2 != i0) {
-                    uint16_t pr = W.pivrow[i2];
-                    if (pr != kNone) lv = max(lv, (int)W.lb[pr]);
-                }
-            }
-            lv = (int)__reduce_max_sync(kFull, (unsigned)lv) + 1;
-            if (lane == 0) W.lb[r] = (uint16_t)lv;
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    // level buckets (counting sort) for both solves; pivot signs
+__device__ inline Levels finish_levels(Blk& B, const CodeView& C, WS<T>& W, const Frame& F) {
+    const int n = C.n, p = F.p;
     int mb = 0, mf = 0;
     for (int r = B.tid; r < p; r += B.nt) {
         mb = max(mb, (int)W.lb[r]);
@@ -608,9 +600,9 @@ __device__ inline Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const F
         int i0 = W.pivcol[r];
         uint8_t s = 0;
         if (i0 < n) {
-            for (int k = C.v_ptr[i0]; k < C.v_ptr[i0 + 1]; ++k) {
-                uint16_t ent = W.colent[k];
-                if (ent != kNone && (ent & kIdx) == r) s = (ent & kNeg) ? 1 : 0;
+            for (uint32_t e = W.rptr[r]; e < W.rptr[r + 1]; ++e) {
+                uint16_t ent = W.rowent[e];
+                if ((ent & kIdx) == i0) s = (ent & kNeg) ? 1 : 0;
             }
         }
         W.psgn[r] = s;
@@ -646,6 +638,122 @@ __device__ inline Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const F
     __syncthreads();
     build_deps<T>(B, C, W, F);
     return L;
+}
+
+// Ranks the q columns by (weight desc, index asc): rank[i], sorted[k].
+template <typename T>
+__device__ inline void rank_columns(Blk& B, WS<T>& W, const Frame& F, const double* wt) {
+    const int q = F.q;
+    int q2 = 1;
+    while (q2 < q) q2 <<= 1;
+    for (int k = B.tid; k < q2; k += B.nt)
+        W.skey[k] = (k < q) ? (((unsigned long long)desc_key32((float)wt[k]) << 32) | (unsigned)k)
+                            : ~0ull;
+    __syncthreads();
+    bitonic_sort(B, W.skey, q2);
+    for (int k = B.tid; k < q; k += B.nt) {
+        int i = (int)(W.skey[k] & 0xffffffffu);
+        W.rank[i] = (uint16_t)k;
+        W.sorted[k] = (uint16_t)i;
+    }
+    __syncthreads();
+}
+
+// Back-substitution levels of an upper-triangular order, in reverse
+// selection order selrow[p-1..0], on warp B.sw (every other warp returns).
+template <typename T>
+__device__ inline void back_levels(Blk& B, WS<T>& W, int p) {
+    if (B.warp != B.sw) return;
+    for (int k = p - 1; k >= 0; --k) {
+        int r = W.selrow[k];
+        int i0 = W.pivcol[r];
+        int lv = 0;
+        const int e0 = (int)W.rptr[r], d = (int)W.rptr[r + 1] - e0;
+        for (int t = B.lane; t < d; t += 32) {
+            int i2 = W.rowent[e0 + t] & kIdx;
+            if (i2 != i0) {
+                uint16_t pr = W.pivrow[i2];
+                if (pr != kNone) lv = max(lv, (int)W.lb[pr]);
+            }
+        }
+        lv = (int)__reduce_max_sync(kFull, (unsigned)lv) + 1;
+        if (B.lane == 0) W.lb[r] = (uint16_t)lv;
+        __syncwarp();
+    }
+}
+
+template <typename T>
+__device__ inline Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                                    const double* wt, int /*q2*/) {
+    const int n = C.n, p = F.p, q = F.q;
+    for (int i = B.tid; i < q; i += B.nt) {
+        W.deg[i] = (uint16_t)(i < n ? (int)(W.cptr[i + 1] - W.cptr[i]) : 1);
+        W.pivrow[i] = kNone;
+    }
+    for (int r = B.tid; r < p; r += B.nt) { W.pivcol[r] = kNone; W.lb[r] = 1; W.lf[r] = 1; }
+    rank_columns<T>(B, W, F, wt);   // (barriers inside)
+    const int nw = (q + 31) / 32;
+    for (int k = B.tid; k < nw; k += B.nt) W.bitmap[k] = 0;
+    __syncthreads();
+    for (int i = B.tid; i < q; i += B.nt)
+        if (W.deg[i] == 1) atomicOr(&W.bitmap[W.rank[i] >> 5], 1u << (W.rank[i] & 31));
+    __syncthreads();
+
+    if (B.warp == B.sw) {
+        const int lane = B.lane;
+        for (int k = 0; k < p; ++k) {
+            unsigned best = 0xffffffffu;
+            for (int wd = lane; wd < nw; wd += 32) {
+                uint32_t v = W.bitmap[wd];
+                if (v) { best = (unsigned)(wd * 32 + __ffs(v) - 1); break; }
+            }
+            best = __reduce_min_sync(kFull, best);
+            if (best >= (unsigned)q) break;   // cannot happen: every live row keeps its slack
+            int i = W.sorted[best];
+            int jr, lev;
+            if (i >= n) {
+                jr = i - n;
+                lev = 1;
+            } else {
+                const int beg = (int)W.cptr[i], d = (int)W.cptr[i + 1] - beg;
+                unsigned cand = 0xffffffffu;
+                int lv = 0;
+                for (int t = lane; t < d; t += 32) {
+                    int r = W.colent[beg + t] & kIdx;
+                    if (W.pivcol[r] == kNone) cand = min(cand, (unsigned)r);
+                    else lv = max(lv, (int)W.lf[r]);
+                }
+                unsigned jm = __reduce_min_sync(kFull, cand);
+                lev = (int)__reduce_max_sync(kFull, (unsigned)lv) + 1;
+                if (jm >= (unsigned)p) break;  // cannot happen: i has degree one
+                jr = (int)jm;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                W.pivcol[jr] = (uint16_t)i;
+                W.pivrow[i] = (uint16_t)jr;
+                W.lf[jr] = (uint16_t)lev;
+                W.selrow[k] = (uint16_t)jr;
+                atomicAnd(&W.bitmap[best >> 5], ~(1u << (best & 31)));
+            }
+            __syncwarp();
+            // zero row jr: every other live column of the row loses one degree
+            const int e0 = (int)W.rptr[jr], d = (int)W.rptr[jr + 1] - e0;
+            for (int t = lane; t <= d; t += 32) {
+                int i2 = (t < d) ? (W.rowent[e0 + t] & kIdx) : n + jr;
+                if (W.pivrow[i2] != kNone) continue;   // taken (includes i)
+                int nd = (int)W.deg[i2] - 1;
+                W.deg[i2] = (uint16_t)nd;
+                int rk = W.rank[i2];
+                if (nd == 1) atomicOr(&W.bitmap[rk >> 5], 1u << (rk & 31));
+                else if (nd == 0) atomicAnd(&W.bitmap[rk >> 5], ~(1u << (rk & 31)));
+            }
+            __syncwarp();
+        }
+        back_levels<T>(B, W, p);
+    }
+    __syncthreads();
+    return finish_levels<T>(B, C, W, F);
 }
 
 // Selection order as (column, row) pairs, for the step entry point.
@@ -951,12 +1059,22 @@ __device__ inline int pcg_m32(Blk& B, const CodeView& C, WS<T>& W, const Frame& 
 // (FP32 cannot resolve the preconditioned system once D^2 spreads over many
 // decades near the optimum). Stops at ||r64|| < tol ||w||, when an FP64
 // round no longer halves ||r64||, or when the PCG budget is spent.
-struct NewtonOut { int iters, iters64, dense; double relres, flops; };
+struct NewtonOut { int iters, iters64, dense; double relres, flops, bytes; };
 
 // Algorithmic floating-point operations of one PCG iteration (Algorithm 4):
 // Q h (2 passes over the pattern, D^2 and the slacks), the two triangular
 // solves (one multiply-add per dependency, pivot scaling), three dot
 // products and the vector updates.
+// Algorithmic bytes of one PCG iteration, as the survey's roofline counts
+// them for a streamed frame (4-byte indices, FP64 D^2, vectors of rb bytes):
+// Q h reads both index passes (8 E_A), the row list (4p), D^2 (8q) and h,
+// and writes l; each triangular solve reads 4 nnz(A_M) + 8p; two dot
+// products and three vector updates move 5 vectors of 8p.
+__device__ __forceinline__ double pcg_iter_bytes(const Frame& F, int n, int nnz_m, int rb) {
+    const double p = F.p;
+    return 8.0 * F.ea + 4.0 * p + 8.0 * (n + p) + 2.0 * rb * p + 2.0 * (4.0 * nnz_m + 8.0 * p) +
+           40.0 * p;
+}
 __device__ __forceinline__ double pcg_iter_flops(const Frame& F, int n, int deps) {
     return 4.0 * F.ea + 2.0 * deps + n + 15.0 * F.p;
 }
@@ -1022,14 +1140,12 @@ __device__ inline bool dense_newton(Blk& B, const CodeView& C, WS<T>& W, const F
     // A(r,i) A(r2,i) d_i^2, plus d^2 of row r's slack on the diagonal; thread
     // r writes only row r (entries (r2, r) of column r2), in a fixed order
     for (int r = B.tid; r < p; r += B.nt) {
-        const int j = W.rowchk[r];
-        for (int e = C.h_ptr[j]; e < C.h_ptr[j + 1]; ++e) {
+        for (uint32_t e = W.rptr[r]; e < W.rptr[r + 1]; ++e) {
             const uint16_t ent = W.rowent[e];
             const int i = ent & kIdx;
             const double dd = W.d2[i];
-            for (int k = C.v_ptr[i]; k < C.v_ptr[i + 1]; ++k) {
+            for (uint32_t k = W.cptr[i]; k < W.cptr[i + 1]; ++k) {
                 const uint16_t ce = W.colent[k];
-                if (ce == kNone) continue;
                 const int r2 = ce & kIdx;
                 Lm[(size_t)r2 * p + r] += ((ent ^ ce) & kNeg) ? -dd : dd;
             }
@@ -1090,11 +1206,13 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
     double ww = 0.0;
     for (int r = B.tid; r < p; r += B.nt) { W.dy[r] = 0.0; W.r64[r] = W.w[r]; ww += W.w[r] * W.w[r]; }
     const double wn = sqrt(bsum(B, ww));
-    NewtonOut o{0, 0, 0, 0.0, 0.0};
+    NewtonOut o{0, 0, 0, 0.0, 0.0, 0.0};
     if (wn == 0.0) return o;
     const double it_flops = pcg_iter_flops(F, C.n, (int)(W.bptr[p] + W.fptr[p]));
+    const int nnz_m = p + (int)W.bptr[p];
     double rn = wn;
-    if (force_dense && dense_newton<T>(B, C, W, F)) {   // PCG already failed in this LP
+    const bool dense_ok = W.qd != nullptr && F.p <= W.dense_p;
+    if (force_dense && dense_ok && dense_newton<T>(B, C, W, F)) {   // PCG already failed in this LP
         double rr;
         residual64<double, T>(B, C, W, F, &rr);
         o.dense = 1;
@@ -1126,7 +1244,7 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
             if (!m32) o.iters64 += it;
         } else {
             if (!view_ready) {
-                W64 = fp64_view<T>(W, C.n, C.m);
+                W64 = fp64_view<T>(W);
                 for (int r = B.tid; r < p; r += B.nt) W64.invd2p[r] = 1.0 / W.d2[W.pivcol[r]];
                 __syncthreads();
                 view_ready = true;
@@ -1136,6 +1254,7 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
         }
         o.iters += it;
         o.flops += it * it_flops + 4.0 * F.ea + C.n + 3.0 * p;
+        o.bytes += it * pcg_iter_bytes(F, C.n, nnz_m, use64 ? 8 : (int)sizeof(T));
         double rr;
         residual64<double, T>(B, C, W, F, &rr);
         double rn_new = sqrt(rr);
@@ -1151,7 +1270,7 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
         }
     }
     o.relres = rn / wn;
-    if (o.relres > tol && W.qd != nullptr) {   // PCG stalled: direct solve, for the rest of the LP
+    if (o.relres > tol && dense_ok) {   // PCG stalled: direct solve, for the rest of the LP
         force_dense = true;
         if (dense_newton<T>(B, C, W, F)) {
             double rr;
@@ -1179,10 +1298,9 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
 template <typename T>
 __device__ __forceinline__ double rowA_basic(const CodeView& C, const WS<T>& W, int r,
                                              const double* v) {
-    int j = W.rowchk[r];
     double acc = 0.0;
-    const int e1 = C.h_ptr[j + 1];
-    for (int e = C.h_ptr[j]; e < e1; ++e) {
+    const uint32_t e1 = W.rptr[r + 1];
+    for (uint32_t e = W.rptr[r]; e < e1; ++e) {
         uint16_t ent = W.rowent[e];
         int i = ent & kIdx;
         if (W.basic[i]) acc += signed_val<double>(ent, v[i]);
@@ -1335,7 +1453,7 @@ template <typename T>
 __device__ inline int certify_basis(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                     const Levels& L, const double* gamma) {
     const int n = C.n, p = F.p, q = F.q;
-    WS<double> D = fp64_view<T>(W, n, C.m);
+    WS<double> D = fp64_view<T>(W);
     double* rhs = W.vr1;
     double* out = W.vr2;
     double cmax = 0.0;
@@ -1384,7 +1502,7 @@ __device__ inline int certify_basis(Blk& B, const CodeView& C, WS<T>& W, const F
 // ---------------------------------------------------------------------------
 struct IpmOut {
     int iters, pcg_iters, pcg_iters64, converged, certified, max_levels, dense;
-    double flops;
+    double flops, bytes;
 };
 
 // trace (optional): per iteration 8 doubles {gap, feas_p, feas_d, PCG
@@ -1394,7 +1512,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
                                    const DevParams& P, const double* gamma, int q2,
                                    double* trace = nullptr, int max_trace = 0) {
     const int n = C.n, p = F.p, q = F.q;
-    IpmOut o{0, 0, 0, 0, 0, 0, 0, 0.0};
+    IpmOut o{0, 0, 0, 0, 0, 0, 0, 0.0, 0.0};
     // cold start x = e, y = 0, z = c + e
     double nc2 = 0.0;
     for (int i = B.tid; i < q; i += B.nt) {
@@ -1495,6 +1613,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
         o.pcg_iters += no.iters;
         o.pcg_iters64 += no.iters64;
         o.flops += no.flops;
+        o.bytes += no.bytes;
         last_pcg = no.dense ? 1000000 : no.iters;
         if (no.relres > 1e-3 && g_rel < 1e-6) {   // no usable direction left near the optimum
             o.iters = it;
@@ -1561,9 +1680,8 @@ __device__ inline int vertex_recover(Blk& B, const CodeView& C, WS<T>& W, const 
     __syncthreads();
     double ss = 0.0, nb_ = 0.0;
     for (int r = B.tid; r < p; r += B.nt) {   // s = b - A_B x_B
-        int j = W.rowchk[r];
         double acc = 0.0;
-        for (int e = C.h_ptr[j]; e < C.h_ptr[j + 1]; ++e) {
+        for (uint32_t e = W.rptr[r]; e < W.rptr[r + 1]; ++e) {
             uint16_t ent = W.rowent[e];
             int i = ent & kIdx;
             if (W.basic[i]) acc += signed_val<double>(ent, W.x[i]);
@@ -1647,9 +1765,12 @@ template <typename T>
 __device__ inline void lp_finish(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                  const DevParams& P) {
     for (int i = B.tid; i < C.n; i += B.nt) W.u[i] = flipped(W.flip, i) ? 1.0 - W.x[i] : W.x[i];
-    for (int r = B.tid; r < F.p; r += B.nt) {
-        int j = W.rowchk[r];
-        W.flags[j] = kInLP | ((W.x[C.n + r] <= P.tau_act) ? kActive : 0);
+    for (int r = B.tid; r < F.p; r += B.nt) W.cact[r] = (W.x[C.n + r] <= P.tau_act) ? 1 : 0;
+    __syncthreads();
+    for (int j = B.tid; j < C.m; j += B.nt) {
+        uint8_t f = 0;
+        for (uint32_t r = W.crptr[j]; r < W.crptr[j + 1]; ++r) f |= W.cact[r] ? kActive : 0;
+        if (W.crptr[j + 1] > W.crptr[j]) W.flags[j] = kInLP | f;
     }
     __syncthreads();
 }
@@ -1688,23 +1809,29 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
     bad = __syncthreads_or(bad);
     Frame F{0, C.n, 0.0, 0.0, 0};
     lpdec_stats st{};
+    st.t_start = (double)t0;
     if (bad) {
         st.status = LPDEC_ERR_INVALID_ARG;
         for (int i = B.tid; i < C.n; i += B.nt) { out.u[i] = NAN; out.hard[i] = 0; }
         if (out.mask) for (int j = B.tid; j < C.m; j += B.nt) out.mask[j] = 0;
-        if (B.tid == 0) { *out.cert = 0; if (out.stats) *out.stats = st; }
+        if (B.tid == 0) {
+            *out.cert = 0;
+            st.t_end = (double)global_ns();
+            if (out.stats) *out.stats = st;
+        }
         __syncthreads();
         return;
     }
     frame_init<T>(B, C, W, gamma);
     int status = LPDEC_OK;
     double cost = frame_cost(B, C, W, gamma);    // gamma'u^0
+    bool alp = P.variant == LPDEC_ALP;           // Algorithm 1 semantics
     for (;;) {
-        if (P.variant == LPDEC_MALP_B) drop_inactive<T>(B, C, W);
-        int added = cut_search<T>(B, C, W, P);
+        if (P.variant == LPDEC_MALP_B && !alp) drop_inactive<T>(B, C, W);
+        int added = cut_search<T>(B, C, W, P, alp);
         if (!added) break;
         if (st.alp_iters >= P.max_alp) { status = LPDEC_ERR_NOT_CONVERGED; break; }
-        lp_build<T>(B, C, W, F, shscan);
+        if (!lp_build<T>(B, C, W, F, shscan, alp)) { status = LPDEC_ERR_OUT_OF_BUDGET; break; }
         IpmOut io = ipm_solve<T>(B, C, W, F, P, gamma, q2);
         st.alp_iters++;
         st.ipm_iters_total += io.iters;
@@ -1712,20 +1839,28 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
         st.pcg_iters_fp64 += io.pcg_iters64;
         st.dense_solves += io.dense;
         st.pcg_flops += io.flops;
+        st.pcg_bytes += io.bytes;
         st.max_levels = max(st.max_levels, io.max_levels);
         int ok = io.certified || certify<T>(B, C, W, F, gamma);
         if (!ok) st.vertex_failures += vertex_recover<T>(B, C, W, F, gamma);
         lp_finish<T>(B, C, W, F, P);
         st.lp_rows_final = F.p;
         if (!io.converged && !ok) { status = LPDEC_ERR_NOT_CONVERGED; break; }
-        // Theorem 2(b): with unique LP optima the cost rises strictly; a
-        // cost that does not rise means the loop may cycle between cut sets.
+        // Theorem 2(b): with unique LP optima the MALP cost rises strictly. A
+        // cost that does not rise means that hypothesis failed and MALP may
+        // cycle between cut sets short of the optimum; the frame continues as
+        // ALP (Algorithm 1), which only adds inequalities and reaches the LP
+        // decoding optimum (Theorem 2(c)).
         const double next = frame_cost(B, C, W, gamma);
-        if (next - cost <= P.tau_inc * (1.0 + fabs(cost))) { status = LPDEC_ERR_STALLED; break; }
+        if (!alp && next - cost <= P.tau_inc * (1.0 + fabs(cost))) {
+            alp = true;
+            st.alp_switch = st.alp_iters;
+        }
         cost = next;
     }
     // a7: outputs. cert = integral; hard_i = [u_i > 1/2], the channel's
-    // decision where u_i is within tau_int of 1/2.
+    // decision where u_i is within tau_int of 1/2. mask[j] = V of check j's
+    // latest inequality.
     int frac = 0;
     double obj = 0.0;
     for (int i = B.tid; i < C.n; i += B.nt) {
@@ -1745,7 +1880,9 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
         *out.cert = frac ? 0 : 1;
         st.status = status;
         st.objective = obj;
-        st.seconds = 1e-9 * (double)(global_ns() - t0);
+        const unsigned long long t1 = global_ns();
+        st.seconds = 1e-9 * (double)(t1 - t0);
+        st.t_end = (double)t1;
         if (out.stats) *out.stats = st;
     }
     __syncthreads();

@@ -24,9 +24,9 @@ LPDEC_ERR_TIMEOUT = -4
 LPDEC_ERR_PENDING = -5
 LPDEC_ERR_CUDA = -6
 LPDEC_ERR_NO_DEVICE = -7
-LPDEC_ERR_STALLED = -8
 LPDEC_MALP_A = 0
 LPDEC_MALP_B = 1
+LPDEC_ALP = 2
 LPDEC_FP64 = 0
 LPDEC_MIXED = 1
 LPDEC_M32 = 2
@@ -38,23 +38,24 @@ class lpdec_params(ctypes.Structure):
                  "pcg_gap_factor", "tol_inner", "tol_feas_loose", "tol_cert", "tau_inc")] + \
                [(k, ctypes.c_int32) for k in
                 ("max_alp", "max_ipm", "max_pcg", "variant", "precision",
-                 "threads_per_block", "smem_budget", "reserved")]
+                 "threads_per_block", "smem_budget", "lp_rows_cap")] + \
+               [("reserved", ctypes.c_int32 * 3)]
 
 
 class lpdec_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in
                 ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total", "lp_rows_final",
-                 "vertex_failures", "max_levels", "pcg_iters_fp64", "dense_solves", "reserved")] + \
-               [("objective", ctypes.c_double), ("pcg_flops", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                 "vertex_failures", "max_levels", "pcg_iters_fp64", "dense_solves", "alp_switch")] + \
+               [(k, ctypes.c_double) for k in
+                ("objective", "pcg_flops", "seconds", "pcg_bytes", "t_start", "t_end")]
 
 
 STATS_DTYPE = np.dtype([(k, np.int32) for k in
                         ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total",
                          "lp_rows_final", "vertex_failures", "max_levels", "pcg_iters_fp64",
-                         "dense_solves", "reserved")] +
-                       [("objective", np.float64), ("pcg_flops", np.float64),
-                        ("seconds", np.float64)])
+                         "dense_solves", "alp_switch")] +
+                       [(k, np.float64) for k in
+                        ("objective", "pcg_flops", "seconds", "pcg_bytes", "t_start", "t_end")])
 assert STATS_DTYPE.itemsize == ctypes.sizeof(lpdec_stats)
 
 
@@ -94,7 +95,9 @@ def _load():
     lib.lpdec_code_destroy.argtypes = [P]
     lib.lpdec_code_destroy.restype = None
     lib.lpdec_decode.argtypes = [P, P, P, P, P, P, P, P]
-    lib.lpdec_decode_batch.argtypes = [P, P, i32, P, P, P, P, P, P]
+    lib.lpdec_decode_frames.argtypes = [P, P, i32, P, P, P, P, P, P]
+    lib.lpdec_decode_batch.argtypes = [P, i32, P, P, P, P, P, P, P]
+    lib.lpdec_decode_mixed_device.argtypes = [P, i32, P, P, P, P, P, P, P, P]
     lib.lpdec_decode_batch_device.argtypes = [P, P, i32, P, P, P, P, P, P, P]
     lib.lpdec_cut_search_device.argtypes = [P, P, i32, P, P, P, P, P, P]
     lib.lpdec_mts_select_device.argtypes = [P, P, i32, P, P, P, P, P, P, P]
@@ -111,7 +114,8 @@ def _load():
     for name in ("lpdec_server_create", "lpdec_submit", "lpdec_poll", "lpdec_server_destroy"):
         getattr(lib, name).restype = i32
     for name in ("lpdec_ctx_create", "lpdec_ctx_set_params", "lpdec_code_create",
-                 "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_batch_device",
+                 "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_frames",
+                 "lpdec_decode_mixed_device", "lpdec_decode_batch_device",
                  "lpdec_cut_search_device", "lpdec_mts_select_device", "lpdec_pcg_device",
                  "lpdec_lp_solve_device", "lpdec_lp_solve_trace_device",
                  "lpdec_decode_batch_device_noalloc"):
@@ -220,12 +224,42 @@ def lpdec_decode(ctx, code, gamma, u_out, hard_out, cert_out, cut_mask_out=None,
                                 _hptr(cut_mask_out, np.uint32), _hptr(stats, STATS_DTYPE))
 
 
-def lpdec_decode_batch(ctx, code, nframes, gamma, u_out, hard_out, cert_out,
-                       cut_mask_out=None, stats=None) -> int:
-    return _load().lpdec_decode_batch(ctx, code, nframes, _hptr(gamma, np.float64),
-                                      _hptr(u_out, np.float64), _hptr(hard_out, np.uint8),
-                                      _hptr(cert_out, np.int32), _hptr(cut_mask_out, np.uint32),
-                                      _hptr(stats, STATS_DTYPE))
+def lpdec_decode_frames(ctx, code, nframes, gamma, u_out, hard_out, cert_out,
+                        cut_mask_out=None, stats=None) -> int:
+    return _load().lpdec_decode_frames(ctx, code, nframes, _hptr(gamma, np.float64),
+                                       _hptr(u_out, np.float64), _hptr(hard_out, np.uint8),
+                                       _hptr(cert_out, np.int32), _hptr(cut_mask_out, np.uint32),
+                                       _hptr(stats, STATS_DTYPE))
+
+
+def _ptr_array(arrays, dtype):
+    """C array of host pointers (NULL entries for None) of 1-D numpy arrays."""
+    out = (ctypes.c_void_p * len(arrays))()
+    for k, a in enumerate(arrays):
+        out[k] = _hptr(a, dtype)
+    return out
+
+
+def lpdec_decode_batch(ctx, codes, gammas, u_out, hard_out, cert_out, cut_mask_out=None,
+                       stats=None) -> int:
+    """Per-frame codes (list of handles) and per-frame host arrays (lists of
+    1-D numpy arrays); cert_out / stats one entry per frame."""
+    nf = len(codes)
+    ch = (ctypes.c_void_p * nf)(*codes)
+    return _load().lpdec_decode_batch(
+        ctx, nf, ch, _ptr_array(gammas, np.float64), _ptr_array(u_out, np.float64),
+        _ptr_array(hard_out, np.uint8), _hptr(cert_out, np.int32),
+        None if cut_mask_out is None else _ptr_array(cut_mask_out, np.uint32),
+        _hptr(stats, STATS_DTYPE))
+
+
+def lpdec_decode_mixed_device(ctx, codes, d_gamma, d_u, d_hard, d_cert, d_cut_mask=None,
+                              d_stats=None, stream=None) -> int:
+    nf = len(codes)
+    ch = (ctypes.c_void_p * nf)(*codes)
+    return _load().lpdec_decode_mixed_device(ctx, nf, ch, _dptr(d_gamma), _dptr(d_u),
+                                             _dptr(d_hard), _dptr(d_cert), _dptr(d_cut_mask),
+                                             _dptr(d_stats), _stream(stream))
 
 
 def lpdec_decode_batch_device(ctx, code, nframes, d_gamma, d_u, d_hard, d_cert,
@@ -298,6 +332,8 @@ class Decoder:
         except Exception:
             lpdec_ctx_destroy(self.ctx)
             raise
+        self.extra = []
+        self.m_of = {self.code: self.m}
 
     def set_params(self, params: lpdec_params):
         self.params = params
@@ -312,11 +348,43 @@ class Decoder:
         cert = np.empty(nf, np.int32)
         masks = np.empty((nf, self.m), np.uint32)
         stats = np.empty(nf, STATS_DTYPE)
-        _check(lpdec_decode_batch(self.ctx, self.code, nf, gamma, u, hard, cert, masks, stats),
+        _check(lpdec_decode_frames(self.ctx, self.code, nf, gamma, u, hard, cert, masks, stats),
+               "lpdec_decode_frames")
+        return u, hard, cert, masks, stats
+
+    def add_code(self, code) -> int:
+        """Uploads another code on this context; returns its handle (freed by
+        close())."""
+        h = lpdec_code_create(self.ctx, int(code.m), int(code.n),
+                              np.ascontiguousarray(code.row_ptr, dtype=np.int32),
+                              np.ascontiguousarray(code.col_idx, dtype=np.int32))
+        self.extra.append(h)
+        self.m_of[h] = int(code.m)
+        return h
+
+    def decode_mixed(self, handles, gammas):
+        """lpdec_decode_batch over frames of several codes: handles[f] and
+        gammas[f] (1-D). Returns lists (u, hard, masks) and arrays (cert,
+        stats)."""
+        nf = len(handles)
+        gammas = [np.ascontiguousarray(g, dtype=np.float64) for g in gammas]
+        ms = [int(m) for m in self._code_m(handles)]
+        u = [np.empty(g.size, np.float64) for g in gammas]
+        hard = [np.empty(g.size, np.uint8) for g in gammas]
+        masks = [np.empty(m, np.uint32) for m in ms]
+        cert = np.empty(nf, np.int32)
+        stats = np.empty(nf, STATS_DTYPE)
+        _check(lpdec_decode_batch(self.ctx, list(handles), gammas, u, hard, cert, masks, stats),
                "lpdec_decode_batch")
         return u, hard, cert, masks, stats
 
+    def _code_m(self, handles):
+        return [self.m_of[h] for h in handles]
+
     def close(self):
+        for h in getattr(self, "extra", []):
+            lpdec_code_destroy(h)
+        self.extra = []
         if self.code:
             lpdec_code_destroy(self.code)
             self.code = None

@@ -24,6 +24,7 @@ def compare_frame(res, u, hard, cert, masks, st, ctx=""):
     assert cert == res.cert, ctx
     assert np.array_equal(masks, res.masks), ctx
     assert st["alp_iters"] == res.alp_iters, ctx
+    assert st["alp_switch"] == res.alp_switch, ctx
     assert st["lp_rows_final"] == res.lp_rows_final, ctx
     assert np.max(np.abs(u - res.u)) <= 1e-6, ctx
     assert abs(st["objective"] - res.objective) <= 1e-6 * (1 + abs(res.objective)), ctx
@@ -72,29 +73,28 @@ def test_decode_edge_cases():
     with L.Decoder(code) as d:
         # empty batch
         e = np.zeros((0, code.n))
-        rc = L.lpdec_decode_batch(d.ctx, d.code, 0, e, np.zeros((0, code.n)),
-                                  np.zeros((0, code.n), np.uint8), np.zeros(0, np.int32))
+        rc = L.lpdec_decode_frames(d.ctx, d.code, 0, e, np.zeros((0, code.n)),
+                                   np.zeros((0, code.n), np.uint8), np.zeros(0, np.int32))
         assert rc == 0
         # hard decision already a codeword: no LP is solved
         g = np.abs(awgn_llr_frames(code.n, code.design_rate, 2.0, 0, [0])) + 0.25
         u, hard, cert, masks, st = d.decode_batch(g)
         assert st["alp_iters"][0] == 0 and cert[0] == 1 and not hard.any() and not masks.any()
         # zero LLRs are accepted (treated as gamma >= 0). The LP optimum need
-        # not be unique then and Theorem 2 (strictly increasing cost, hence
-        # termination) assumes it is, so the decoder only owes a defined
-        # status, and the oracle's optimal cost whenever both converge.
+        # not be unique then (Theorem 2 assumes it is), so the decoder owes a
+        # defined status, and the oracle's optimal cost whenever both converge.
         g0 = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, [1])
         g0[0, ::7] = 0.0
         u, hard, cert, masks, st = d.decode_batch(g0)
         res = oracle.decode(code, g0[0])
-        assert st["status"][0] in (L.LPDEC_OK, L.LPDEC_ERR_NOT_CONVERGED, L.LPDEC_ERR_STALLED)
+        assert st["status"][0] in (L.LPDEC_OK, L.LPDEC_ERR_NOT_CONVERGED)
         if st["status"][0] == 0 and res.status == 0:
             assert abs(st["objective"][0] - res.objective) <= 1e-6 * (1 + abs(res.objective))
         # non-finite LLRs: host entry rejects the call
         bad = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, [2])
         bad[0, 5] = np.nan
-        rc = L.lpdec_decode_batch(d.ctx, d.code, 1, bad, np.zeros((1, code.n)),
-                                  np.zeros((1, code.n), np.uint8), np.zeros(1, np.int32))
+        rc = L.lpdec_decode_frames(d.ctx, d.code, 1, bad, np.zeros((1, code.n)),
+                                   np.zeros((1, code.n), np.uint8), np.zeros(1, np.int32))
         assert rc == L.LPDEC_ERR_INVALID_ARG
         # ... and the device entry flags only that frame
         g2 = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, [3, 4])
@@ -142,10 +142,10 @@ def test_code_create_validates_csr():
         L.lpdec_ctx_destroy(ctx)
 
 
-def test_stall_rule_matches_oracle():
-    """Theorem 2(b) stop rule: with a required cost rise larger than any
-    real one, every frame that needs an LP stops after its first LP with
-    LPDEC_ERR_STALLED, and its outputs are that LP's, as in the oracle."""
+def test_cost_stall_switches_to_alp_as_oracle():
+    """Theorem 2(b) rule: with a required cost rise larger than any real one,
+    every frame that needs an LP continues as ALP (Algorithm 1) after its
+    first LP, and ends, as in the oracle, at the LP decoding optimum."""
     from oracle.params import OracleParams
     torch_cuda()
     code = named_code("gallager_120")
@@ -157,7 +157,95 @@ def test_stall_rule_matches_oracle():
     for f in range(32):
         res = oracle.decode(code, G[f], OracleParams(tau_inc=1e6))
         compare_frame(res, u[f], hard[f], cert[f], masks[f], st[f], f"frame {f}")
-        assert res.alp_iters == 0 or (res.status == L.LPDEC_ERR_STALLED and res.alp_iters == 1)
+        assert res.alp_iters == 0 or res.alp_switch == 1
+
+
+def test_alp_matches_oracle():
+    """ALP (Algorithm 1: inequalities are only added, every check is searched
+    in every round; several inequalities per check) against the oracle's
+    ALP."""
+    from oracle.params import OracleParams
+    torch_cuda()
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(100))
+    prm = L.lpdec_default_params()
+    prm.variant = L.LPDEC_ALP
+    with L.Decoder(code, params=prm) as d:
+        u, hard, cert, masks, st = d.decode_batch(G)
+    more_rows = 0
+    for f in range(100):
+        res = oracle.decode(code, G[f], OracleParams(variant="alp"))
+        compare_frame(res, u[f], hard[f], cert[f], masks[f], st[f], f"frame {f}")
+        more_rows += res.lp_rows_final > len(set(j for j, _ in res.cuts))
+    assert more_rows > 0   # some LP held two inequalities of one check
+
+
+def test_per_frame_failures_leave_the_rest_of_the_batch():
+    """A cap that one frame hits ends only that frame. With max_ipm = 1 a
+    frame that needs an LP ends LPDEC_ERR_NOT_CONVERGED (unless one
+    interior-point step already certifies the optimal vertex, in which case
+    it ends as in the oracle); with a row capacity of 4 every frame whose
+    cut list outgrows it ends LPDEC_ERR_OUT_OF_BUDGET. In both batches the
+    other frames, among them those whose hard decision is a codeword, end
+    with the oracle's result."""
+    torch_cuda()
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(16))
+    G[::3] = np.abs(G[::3]) + 0.25          # every third frame: no LP needed
+    ref = [oracle.decode(code, g) for g in G]
+    assert sum(r.alp_iters == 0 for r in ref) >= 5 and sum(r.alp_iters > 0 for r in ref) >= 5
+    for field, value, status in (("max_ipm", 1, L.LPDEC_ERR_NOT_CONVERGED),
+                                 ("lp_rows_cap", 4, L.LPDEC_ERR_OUT_OF_BUDGET)):
+        prm = L.lpdec_default_params()
+        setattr(prm, field, value)
+        with L.Decoder(code, params=prm) as d:
+            u, hard, cert, masks, st = d.decode_batch(G)
+        failed = 0
+        for f in range(16):
+            rows = max([h.p for h in ref[f].history] or [0])
+            must_fail = (field == "lp_rows_cap" and rows > value)
+            if must_fail or (field == "max_ipm" and st["status"][f] != L.LPDEC_OK):
+                assert st["status"][f] == status, (field, f, st["status"][f])
+                assert ref[f].alp_iters > 0
+                failed += 1
+            else:
+                compare_frame(ref[f], u[f], hard[f], cert[f], masks[f], st[f], f"{field} {f}")
+        assert failed >= 3, field
+
+
+def test_mixed_code_lengths_share_one_launch():
+    """Frames of three codes of different lengths (n = 504, 1008 and 2016)
+    in one batch through lpdec_decode_batch (per-frame codes, one persistent
+    launch over the ragged batch): each frame equals its single-code decode
+    bit for bit, and the n=504 frames also equal the oracle."""
+    torch_cuda()
+    names = ["gallager_504", "peg_1008", "gallager_2016"]
+    codes = [named_code(nm) for nm in names]
+    frames = []
+    for k, c in enumerate(codes):
+        G = awgn_llr_frames(c.n, c.design_rate, 2.5, 40 + k, range(6))
+        frames += [(k, g) for g in G]
+    order = [0, 6, 12, 1, 7, 13, 2, 8, 14, 3, 9, 15, 4, 10, 16, 5, 11, 17]
+    frames = [frames[t] for t in order]
+    with L.Decoder(codes[0]) as d:
+        handles = [d.code, d.add_code(codes[1]), d.add_code(codes[2])]
+        u, hard, cert, masks, st = d.decode_mixed([handles[k] for k, _ in frames],
+                                                  [g for _, g in frames])
+        for k, c in enumerate(codes):
+            idx = [t for t, (kk, _) in enumerate(frames) if kk == k]
+            G = np.stack([frames[t][1] for t in idx])
+            with L.Decoder(c) as d1:
+                u1, h1, c1, m1, s1 = d1.decode_batch(G)
+            for a, t in enumerate(idx):
+                assert np.array_equal(u[t], u1[a]), (names[k], t)
+                assert np.array_equal(hard[t], h1[a]) and cert[t] == c1[a]
+                assert np.array_equal(masks[t], m1[a])
+                for fld in ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total",
+                            "lp_rows_final", "alp_switch", "objective"):
+                    assert st[fld][t] == s1[fld][a], (names[k], t, fld)
+                if k == 0:
+                    res = oracle.decode(c, G[a])
+                    compare_frame(res, u[t], hard[t], cert[t], masks[t], st[t], f"frame {t}")
 
 
 def test_malp_b_matches_oracle():

@@ -1,0 +1,91 @@
+"""Full-size parity against stored oracle decodes (tests/golden/
+peg1008_oracle.json, written by tests/golden/make_peg1008.py, which calls
+only the oracle): the benchmark's (3,6) PEG code n = 1008 at Eb/N0 1.5, 2.0,
+2.5 and 3.0 dB, 64 frames each plus the two 2.0 dB frames whose MALP cost
+stops rising (they continue as ALP). Each SNR's frames are decoded in one
+persistent launch of the device entry point with the library's default
+layout, in each precision mode.
+
+Bar (Section II-B certificate, Theorem 2(c)): status, hard decision,
+certificate, final cut set, number of LPs and of LPs before a switch to
+ALP, and the rows of the last LP bit-exact; u and gamma'u within 1e-6.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_0902_0657_gb300 import lpdec as L
+from synth import awgn_llr_frames, named_code
+
+from .gpu_util import dev, host, torch_cuda
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "peg1008_oracle.json")
+
+
+def load():
+    with open(GOLDEN) as f:
+        doc = json.load(f)
+    code = named_code(doc["code"])
+    rows = doc["frames"]
+    for r in rows:
+        bits = np.frombuffer(bytes.fromhex(r["hard"]), np.uint8)
+        r["hard_v"] = np.unpackbits(bits, bitorder="little")[:code.n]
+        r["masks_v"] = np.array([int(r["masks"][2 * j:2 * j + 2], 16) for j in range(code.m)],
+                                np.uint32)
+        u = r["hard_v"].astype(np.float64)
+        for i, v in r["u_dev"]:
+            u[i] = v
+        r["u_v"] = u
+    return code, doc["seed"], rows
+
+
+def test_golden_file_covers_the_workload():
+    code, seed, rows = load()
+    snrs = sorted({r["ebn0"] for r in rows})
+    assert snrs == [1.5, 2.0, 2.5, 3.0]
+    assert all(sum(r["ebn0"] == e for r in rows) >= 64 for e in snrs)
+    assert sum(r["cert"] == 0 for r in rows) >= 20          # fractional outputs
+    assert sum(r["alp_switch"] > 0 for r in rows) >= 2       # MALP cycles resolved by ALP
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [L.LPDEC_FP64, L.LPDEC_M32, L.LPDEC_MIXED])
+def test_full_size_matches_oracle_goldens(precision):
+    torch = torch_cuda()
+    code, seed, rows = load()
+    prm = L.lpdec_default_params()
+    prm.precision = precision
+    worst_u = 0.0
+    with L.Decoder(code, params=prm) as d:
+        for eb in sorted({r["ebn0"] for r in rows}):
+            grp = [r for r in rows if r["ebn0"] == eb]
+            G = awgn_llr_frames(code.n, code.design_rate, eb, seed, [r["frame"] for r in grp])
+            nf = len(grp)
+            d_u = torch.zeros((nf, code.n), dtype=torch.float64, device="cuda")
+            d_h = torch.zeros((nf, code.n), dtype=torch.uint8, device="cuda")
+            d_c = torch.zeros(nf, dtype=torch.int32, device="cuda")
+            d_m = torch.zeros((nf, code.m), dtype=torch.int32, device="cuda")
+            d_s = torch.zeros(nf * L.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+            rc = L.lpdec_decode_batch_device(d.ctx, d.code, nf, dev(G), d_u, d_h, d_c, d_m, d_s)
+            assert rc == 0, L.error_string(rc)
+            torch.cuda.synchronize()
+            u, h, c = host(d_u), host(d_h), host(d_c)
+            mk, st = host(d_m).view(np.uint32), host(d_s).view(L.STATS_DTYPE)
+            for k, r in enumerate(grp):
+                ctx = (precision, eb, r["frame"])
+                assert st["status"][k] == r["status"], ctx
+                assert np.array_equal(h[k], r["hard_v"]), ctx
+                assert c[k] == r["cert"], ctx
+                assert np.array_equal(mk[k], r["masks_v"]), ctx
+                assert st["alp_iters"][k] == r["alp_iters"], ctx
+                assert st["alp_switch"][k] == r["alp_switch"], ctx
+                assert st["lp_rows_final"][k] == r["lp_rows_final"], ctx
+                du = float(np.max(np.abs(u[k] - r["u_v"])))
+                worst_u = max(worst_u, du)
+                assert du <= 1e-6, (ctx, du)
+                assert abs(st["objective"][k] - r["objective"]) <= \
+                    1e-6 * (1 + abs(r["objective"])), ctx
+    print(f"precision {precision}: max |u - u_oracle| = {worst_u:.3e}")
