@@ -62,6 +62,17 @@ extern "C" {
 #define LPDEC_ALP    2   /* Algorithm 1: inequalities are only added; every check
                             is searched in every round */
 
+/* Preconditioner of the Newton systems (Section V): the maximum-weight
+ * triangular set found by */
+#define LPDEC_MTS_COLUMN      0   /* the column-wise greedy search (Algorithm 7) */
+#define LPDEC_MTS_INCREMENTAL 1   /* the incremental greedy search (Algorithm 6, with the
+                                     triangulation step of Algorithm 5) */
+#define LPDEC_MTS_ROWWISE     2   /* the row-wise greedy search with diagonal expansion
+                                     (Algorithm 8) */
+#define LPDEC_MTS_ADAPTIVE    3   /* column-wise; an LP switches to the incremental search
+                                     for its remaining Newton systems once one needed more
+                                     than precond_switch PCG iterations */
+
 /* Arithmetic of the PCG solve (the IPM state is always FP64). */
 #define LPDEC_FP64  0   /* FP64 PCG */
 #define LPDEC_MIXED 1   /* FP32 PCG inner solves refined against FP64 residuals */
@@ -109,10 +120,14 @@ extern "C" {
  *                     A D^2 A' (LPs of up to 2048 rows), and so are the
  *                     remaining Newton solves of that LP
  *   variant = LPDEC_MALP_A, precision = LPDEC_FP64
- *   lp_rows_cap = 0   rows one frame's LP may hold (0 = m + m/8 for MALP,
- *                     whose LPs hold at most one inequality per check until a
- *                     switch to ALP, and 2m for ALP); a frame whose cut list
- *                     outgrows it ends with LPDEC_ERR_OUT_OF_BUDGET
+ *   precond = LPDEC_MTS_COLUMN, precond_switch = 150
+ *   lp_rows_cap = 0   rows one frame's LP may hold (0 = 2m). The main
+ *                     workspace holds min(m, lp_rows_cap) rows, enough for
+ *                     MALP (one inequality per check); a frame whose cut list
+ *                     grows past it (ALP, or MALP continued as ALP) moves to
+ *                     a wide workspace in global scratch; a frame whose cut
+ *                     list outgrows lp_rows_cap ends with
+ *                     LPDEC_ERR_OUT_OF_BUDGET
  * The decisions are taken on the LP's optimal vertex, recovered from the
  * final interior-point iterate through its strictly complementary
  * partition (basic iff x_i > z_i, Section VI-A) and certified optimal by a
@@ -129,7 +144,10 @@ typedef struct lpdec_params {
     int32_t threads_per_block;  /* 0 = library choice */
     int32_t smem_budget;        /* bytes of shared memory per CTA, 0 = library choice */
     int32_t lp_rows_cap;        /* LP row capacity per frame, 0 = library choice */
-    int32_t reserved[3];
+    int32_t precond;            /* LPDEC_MTS_* */
+    int32_t precond_switch;     /* PCG iterations of one Newton solve after which
+                                   LPDEC_MTS_ADAPTIVE switches the LP to Algorithm 6 */
+    int32_t reserved;
 } lpdec_params;
 
 /* Per-frame results besides u / hard / cert. */
@@ -197,9 +215,9 @@ int32_t lpdec_ctx_set_params(lpdec_ctx* ctx, const lpdec_params* params);
  * Validates the CSR, that every row has 1..32 entries and that
  * m, n <= 32767 (the kernels pack indices into 15 bits). Decoding further
  * needs the arrays that always live in shared memory (about 12 bytes per
- * LP row of capacity, m + m/8 by default, plus one bit per column, see
- * lpdec_workspace_bytes) to fit one CTA's shared memory (227 KB): m up to
- * about 16,000. Larger codes are rejected by the decode calls with
+ * check plus one bit per column, see lpdec_workspace_bytes) to fit one
+ * CTA's shared memory (227 KB): m up to about 18,000. Larger codes are
+ * rejected by the decode calls with
  * LPDEC_ERR_INVALID_ARG. The code may be used with any context on the same
  * device. */
 int32_t lpdec_code_create(lpdec_ctx* ctx, int32_t m, int32_t n,
@@ -337,7 +355,7 @@ int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code,
  *     GPU (other streams, other threads) race on the array: serialize them.
  *   - The dense Cholesky fallback of stalled Newton solves runs as in the
  *     regular entry whenever one CTA's workspace with its matrix fits the
- *     array (n = 1008: about 2.8 MB per CTA, so 11 CTAs run at once instead
+ *     array (n = 1008: about 3.8 MB per CTA, so 8 CTAs run at once instead
  *     of the regular entry's 456); only codes whose matrix alone outgrows the
  *     array run without it, and a frame whose PCG stalls there may end
  *     LPDEC_ERR_NOT_CONVERGED where the regular entry converges.

@@ -14,12 +14,10 @@ matrix T[k, l] = A[row[k], col[l]] is
     incremental (Algorithm 6) and row-wise (Algorithm 8) searches.
 
 Weights: the paper ranks columns by d_i (or alternatively x_i). The oracle
-ranks by d_i^2 = x_i / z_i, which orders columns exactly as d_i does; the
-decoder ranks by d_i^2 rounded to single precision (``f32=True`` here), which
-leaves the selected sets unchanged on the workloads measured and makes the
-ranking keys 32 bits wide. Ties go to the lower column index (standard
-columns 0..n-1 before slack columns n..n+p-1); the row-wise search picks the
-lowest-index degree-1 row.
+ranks by d_i^2 = x_i / z_i in double precision, which orders columns exactly
+as d_i does. Ties go to the lower column index (standard columns 0..n-1
+before slack columns n..n+p-1); the row-wise search picks the lowest-index
+degree-1 row.
 """
 
 from __future__ import annotations
@@ -42,14 +40,12 @@ def _pattern(A):
 # Algorithm 7: column-wise greedy search (upper-triangular A_M)
 # ---------------------------------------------------------------------------
 
-def colwise(A, w, f32: bool = False):
+def colwise(A, w):
     """Algorithm 7. Repeatedly take the maximum-weight degree-1 column of
     the residual matrix, record it with the row of its only nonzero, and zero
     that row. DEG1 is kept in a binary heap (Section V-B) with lazy deletion
     of columns whose degree has dropped to zero."""
     p, q = A.shape
-    if f32:
-        w = np.asarray(w, dtype=np.float64).astype(np.float32).astype(np.float64)
     col_rows, row_cols = _pattern(A)
     deg = np.array([len(r) for r in col_rows], dtype=np.int64)
     row_alive = np.ones(p, dtype=bool)

@@ -55,7 +55,7 @@ __device__ __forceinline__ int next_frame(Blk& B, int* counter, int* slot) {
     if (threadIdx.x == 0) ks.sw = serial_warp(B.nwarps);                        \
     __syncthreads();                                                            \
     B.sw = ks.sw;                                                               \
-    WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.gbytes);
+    WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.stride);
 
 // Where frame f of a batch lives: its code (index into the batch's code
 // table) and the offsets of its bits and checks in the packed (ragged)
@@ -72,10 +72,12 @@ struct FrameDesc {
 template <typename T>
 __global__ void __launch_bounds__(512)
 k_decode(CodeView C0, const CodeView* __restrict__ codes, const FrameDesc* __restrict__ descs,
-         DevParams P, Layout L, const double* __restrict__ gamma, double* u, uint8_t* hard,
-         int32_t* cert, uint32_t* mask, lpdec_stats* stats, int nframes, int* counter,
-         char* gscratch) {
+         DevParams P, Layout L, Layout Lw, const double* __restrict__ gamma, double* u,
+         uint8_t* hard, int32_t* cert, uint32_t* mask, lpdec_stats* stats, int nframes,
+         int* counter, char* gscratch) {
     KERNEL_PROLOGUE
+    char* gw = gscratch + (size_t)blockIdx.x * L.stride + L.gbytes;   // wide workspace
+    const Layout* lw = Lw.gbytes ? &Lw : nullptr;
     CodeView C = descs ? C0 : bind_code<T>(C0, W);
     int bound = -1;
     for (;;) {
@@ -90,7 +92,7 @@ k_decode(CodeView C0, const CodeView* __restrict__ codes, const FrameDesc* __res
         }
         FrameOut o{u + on, hard + on, cert + f, mask ? mask + om : nullptr,
                    stats ? stats + f : nullptr};
-        decode_frame<T>(B, C, W, P, gamma + on, o, 0, ks.shscan);
+        decode_frame<T>(B, C, W, P, gamma + on, o, 0, ks.shscan, lw, gw);
     }
 }
 
@@ -159,10 +161,11 @@ k_mts_select(CodeView C0, DevParams P, Layout L, const double* gamma, const uint
         load_lp_state<T>(B, C, W, gamma + (size_t)f * C.n, in_lp + (size_t)f * C.m,
                          mask + (size_t)f * C.m);
         Frame F{0, C.n, 0.0, 0.0, 0};
-        lp_build<T>(B, C, W, F, ks.shscan, false);
+        lp_build<T>(B, C, W, F, ks.shscan, false, C.pmax, C.eamax);
         for (int i = B.tid; i < F.q; i += B.nt) W.d2[i] = wts[(size_t)f * qm + i];
         __syncthreads();
-        mts_select<T>(B, C, W, F, W.d2, 0);
+        select_mts<T>(B, C, W, F, W.d2, P.precond == LPDEC_MTS_ADAPTIVE ? LPDEC_MTS_COLUMN
+                                                                          : P.precond);
         selection_order<T>(B, W, F, col + (size_t)f * C.m, row + (size_t)f * C.m, C.m);
         __syncthreads();
     }
@@ -182,11 +185,12 @@ k_pcg(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in
         load_lp_state<T>(B, C, W, gamma + (size_t)f * C.n, in_lp + (size_t)f * C.m,
                          mask + (size_t)f * C.m);
         Frame F{0, C.n, 0.0, 0.0, 0};
-        lp_build<T>(B, C, W, F, ks.shscan, false);
+        lp_build<T>(B, C, W, F, ks.shscan, false, C.pmax, C.eamax);
         for (int i = B.tid; i < F.q; i += B.nt) W.d2[i] = d2[(size_t)f * qm + i];
         for (int r = B.tid; r < F.p; r += B.nt) W.w[r] = wv[(size_t)f * C.m + r];
         __syncthreads();
-        Levels Lv = mts_select<T>(B, C, W, F, W.d2, 0);
+        Levels Lv = select_mts<T>(B, C, W, F, W.d2,
+                                  P.precond == LPDEC_MTS_ADAPTIVE ? LPDEC_MTS_COLUMN : P.precond);
         for (int i = B.tid; i < F.q; i += B.nt) W.d2t[i] = (T)W.d2[i];
         for (int r = B.tid; r < F.p; r += B.nt) W.invd2p[r] = (T)(1.0 / W.d2[W.pivcol[r]]);
         __syncthreads();
@@ -214,7 +218,7 @@ k_lp_solve(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_
         const double* g = gamma + (size_t)f * C.n;
         load_lp_state<T>(B, C, W, g, in_lp + (size_t)f * C.m, mask + (size_t)f * C.m);
         Frame F{0, C.n, 0.0, 0.0, 0};
-        lp_build<T>(B, C, W, F, ks.shscan, false);
+        lp_build<T>(B, C, W, F, ks.shscan, false, C.pmax, C.eamax);
         lpdec_stats st{};
         if (F.p > 0) {
             IpmOut io = ipm_solve<T>(B, C, W, F, P, g, 0,
@@ -304,16 +308,17 @@ DevParams to_dev(const lpdec_params& p) {
     d.tau_inc = p.tau_inc;
     d.max_alp = p.max_alp; d.max_ipm = p.max_ipm; d.max_pcg = p.max_pcg;
     d.variant = p.variant; d.precision = p.precision;
+    d.precond = p.precond; d.precond_switch = p.precond_switch;
     return d;
 }
 
-// LP row capacity of one frame (lp_rows_cap; library choice: m + m/8 for
-// MALP, whose LPs hold one inequality per check until a frame continues as
-// ALP, 2m for ALP). Row indices are packed in 15 bits and column indices
-// n + r in 16.
+// LP row capacity of one frame (lp_rows_cap; library choice: 2m). The main
+// workspace holds min(m, cap) rows, enough for MALP (one row per check); a
+// frame whose cut list grows past it (ALP, or MALP continued as ALP) moves
+// to a wide workspace in global scratch. Row indices are packed in 15 bits
+// and column indices n + r in 16.
 int rows_cap(const lpdec_params& prm, int n, int m) {
-    long long cap = prm.lp_rows_cap > 0 ? prm.lp_rows_cap
-                  : (prm.variant == LPDEC_ALP ? 2LL * m : (long long)m + (m + 7) / 8);
+    long long cap = prm.lp_rows_cap > 0 ? prm.lp_rows_cap : 2LL * m;
     cap = std::min<long long>({cap, 32767LL, 65535LL - n});
     return (int)std::max<long long>(cap, 1);
 }
@@ -321,8 +326,10 @@ int rows_cap(const lpdec_params& prm, int n, int m) {
 CodeView view_of(const lpdec_code* c, const lpdec_params& prm) {
     CodeView v;
     v.n = c->n; v.m = c->m; v.E = c->E;
-    v.pmax = rows_cap(prm, c->n, c->m);
+    v.pwide = rows_cap(prm, c->n, c->m);
+    v.pmax = std::min(v.pwide, c->m);   // MALP: one row per check
     v.eamax = v.pmax * c->dmax;
+    v.eawide = v.pwide * c->dmax;
     v.h_ptr = c->h_ptr; v.h_col = c->h_col; v.e_chk = c->e_chk;
     v.v_ptr = c->v_ptr; v.v_chk = c->v_chk; v.v_eidx = c->v_eidx;
     return v;
@@ -353,10 +360,11 @@ bool layout_ok(const Layout& L, const std::vector<size_t>& sizes) {
 
 // Capacities one workspace is laid out for: the largest code of a launch.
 struct Dims {
-    int n = 0, m = 0, pmax = 0, eamax = 0;
+    int n = 0, m = 0, pmax = 0, eamax = 0, pwide = 0, eawide = 0;
     void cover(const CodeView& v) {
         n = std::max(n, v.n); m = std::max(m, v.m);
         pmax = std::max(pmax, v.pmax); eamax = std::max(eamax, v.eamax);
+        pwide = std::max(pwide, v.pwide); eawide = std::max(eawide, v.eawide);
     }
 };
 
@@ -370,13 +378,14 @@ constexpr int kDenseMaxRows = 2048;
 // with shared-memory atomics, always do. The FP64 interior-point state goes
 // to per-CTA global scratch. dense_rows = capacity of the dense fallback's
 // matrix (0 = fallback off).
-Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, int dense_rows) {
+Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, int dense_rows,
+                   bool all_global = false) {
     const int n = d.n, m = d.m, pm = d.pmax;
     const size_t ea = (size_t)std::max(d.eamax, 1);
     const size_t q = (size_t)n + pm;
     size_t q2 = 1;
     while (q2 < q) q2 <<= 1;
-    const size_t vec = std::max(vec_bytes(n, pm, real_bytes, m32), 8 * q2 + 4 * q);
+    const size_t vec = std::max(vec_bytes(n, pm, real_bytes, m32), 12 * q2 + 4 * q);
     struct Spec { int id; size_t bytes; int where; };  // 0 = budgeted, 1 = always shared, 2 = global
     const size_t D = 8, I = 4, H = 2, P = (size_t)pm;
     std::vector<Spec> specs = {
@@ -412,7 +421,7 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
     for (const auto& sp : specs) {
         size_t b = align_up(sp.bytes, 16);
         sizes[sp.id] = sp.bytes;
-        if (sp.where == 1 || (sp.where == 0 && s + b <= budget)) {
+        if (!all_global && (sp.where == 1 || (sp.where == 0 && s + b <= budget))) {
             L.off[sp.id] = (uint32_t)s;
             s += b;
         } else {
@@ -427,15 +436,43 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
     L.mmax = (uint32_t)m;
     L.pmax = (uint32_t)pm;
     L.gbytes = align_up(g, 256);
+    L.stride = L.gbytes;
     if (specs.size() != (size_t)A_COUNT || !layout_ok(L, sizes) || g >= kGlobalBit)
         L.smem_bytes = 0xffffffffu;
     return L;
 }
 
-int dense_rows_for(const Dims& d) { return d.pmax <= kDenseMaxRows ? d.pmax : 0; }
+// Rows of the dense fallback's matrix: the main capacity and a quarter more
+// (frames continued as ALP), at most 2048.
+int dense_rows_for(const Dims& d) {
+    return std::min({d.pmax + d.pmax / 4, std::max(d.pwide, d.pmax), kDenseMaxRows});
+}
+
+// The wide workspace (all in global scratch) for frames whose cut list
+// outgrows the main one; gbytes = 0 when the capacity does not exceed it.
+Layout make_wide_layout(const Dims& d, size_t real_bytes, bool m32) {
+    Layout W{};
+    if (d.pwide <= d.pmax) return W;
+    Dims w = d;
+    w.pmax = d.pwide;
+    w.eamax = d.eawide;
+    W = make_layout(w, 0, real_bytes, m32, 0, true);
+    return W;
+}
+
+// Both workspaces of a launch: main (L) then wide (Lw) in each CTA's scratch.
+bool make_layouts(const Dims& d, size_t budget, size_t real_bytes, bool m32, int dense_rows,
+                  Layout* L, Layout* Lw) {
+    *L = make_layout(d, budget, real_bytes, m32, dense_rows);
+    *Lw = make_wide_layout(d, real_bytes, m32);
+    if (L->smem_bytes == 0xffffffffu || Lw->smem_bytes == 0xffffffffu) return false;
+    L->stride = L->gbytes + Lw->gbytes;
+    Lw->stride = L->stride;
+    return true;
+}
 
 struct Launch {
-    Layout L;
+    Layout L, Lw;
     int threads;
     int grid;
 };
@@ -458,9 +495,9 @@ int32_t plan(lpdec_ctx* ctx, const Dims& dims, int nframes, K kernel, size_t rea
              Launch* out) {
     int threads = ctx->prm.threads_per_block > 0 ? ctx->prm.threads_per_block : 128;
     threads = std::max(32, std::min(512, threads / 32 * 32));
-    Layout L = make_layout(dims, smem_budget_of(ctx), real_bytes,
-                           ctx->prm.precision == LPDEC_M32, dense_rows_for(dims));
-    if (L.smem_bytes == 0xffffffffu) {
+    Layout L, Lw;
+    if (!make_layouts(dims, smem_budget_of(ctx), real_bytes, ctx->prm.precision == LPDEC_M32,
+                      dense_rows_for(dims), &L, &Lw)) {
         snprintf(g_err, sizeof g_err, "inconsistent workspace layout");
         return LPDEC_ERR_INVALID_ARG;
     }
@@ -478,8 +515,8 @@ int32_t plan(lpdec_ctx* ctx, const Dims& dims, int nframes, K kernel, size_t rea
     int grid = std::max(1, std::min(nframes, per_sm * ctx->sm_count));
     // scratch for the full grid, whatever this batch needs, so that a small
     // batch (a warm-up) leaves no allocation to a later, larger one
-    size_t need = (size_t)per_sm * ctx->sm_count * L.gbytes;
-    if (ctx->budget && need + ctx->staging_bytes > ctx->budget) need = (size_t)grid * L.gbytes;
+    size_t need = (size_t)per_sm * ctx->sm_count * L.stride;
+    if (ctx->budget && need + ctx->staging_bytes > ctx->budget) need = (size_t)grid * L.stride;
     if (need > ctx->gscratch_bytes) {
         if (ctx->budget && need + ctx->staging_bytes > ctx->budget) return LPDEC_ERR_OUT_OF_BUDGET;
         if (ctx->gscratch) CK(cudaFree(ctx->gscratch));
@@ -489,6 +526,7 @@ int32_t plan(lpdec_ctx* ctx, const Dims& dims, int nframes, K kernel, size_t rea
         ctx->gscratch_bytes = need;
     }
     out->L = L;
+    out->Lw = Lw;
     out->threads = threads;
     out->grid = grid;
     return LPDEC_OK;
@@ -545,6 +583,7 @@ bool params_ok(const lpdec_params& p) {
         return false;
     if (p.precision != LPDEC_FP64 && p.precision != LPDEC_MIXED && p.precision != LPDEC_M32)
         return false;
+    if (p.precond < LPDEC_MTS_COLUMN || p.precond > LPDEC_MTS_ADAPTIVE) return false;
     return p.lp_rows_cap >= 0;
 }
 
@@ -571,11 +610,11 @@ int32_t launch_decode(lpdec_ctx* ctx, const lpdec_code* code, int nframes, const
     CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
     if (mixed)
         k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            cv, nullptr, nullptr, dp, ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
+            cv, nullptr, nullptr, dp, ln.L, ln.Lw, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
             nframes, ctx->counter, ctx->gscratch);
     else
         k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            cv, nullptr, nullptr, dp, ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
+            cv, nullptr, nullptr, dp, ln.L, ln.Lw, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
             nframes, ctx->counter, ctx->gscratch);
     CK(cudaGetLastError());
     return LPDEC_OK;
@@ -629,11 +668,13 @@ int32_t launch_decode_mixed(lpdec_ctx* ctx, int nframes, const lpdec_code* const
     CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
     if (mixed)
         k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            views[0], dv, dd, dp, ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats, nframes,
+            views[0], dv, dd, dp, ln.L, ln.Lw, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
+            nframes,
             ctx->counter, ctx->gscratch);
     else
         k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            views[0], dv, dd, dp, ln.L, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats, nframes,
+            views[0], dv, dd, dp, ln.L, ln.Lw, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
+            nframes,
             ctx->counter, ctx->gscratch);
     CK(cudaGetLastError());
     return LPDEC_OK;
@@ -665,6 +706,8 @@ void lpdec_default_params(lpdec_params* p) {
     p->variant = LPDEC_MALP_A;
     p->precision = LPDEC_FP64;
     p->lp_rows_cap = 0;
+    p->precond = LPDEC_MTS_COLUMN;
+    p->precond_switch = 150;
 }
 
 const char* lpdec_error_string(int32_t code) {
@@ -693,13 +736,18 @@ int32_t lpdec_workspace_bytes(int32_t m, int32_t n, int32_t E, int32_t precision
     Dims d;
     d.n = n;
     d.m = m;
-    d.pmax = rows_cap(prm, n, m);
-    d.eamax = d.pmax * ((E + m - 1) / m);   // check degrees at most ceil(E/m)
-    Layout L = make_layout(d, budget, precision == LPDEC_MIXED ? 4 : 8, precision == LPDEC_M32,
-                           dense_rows_for(d));
+    const int dmax = (E + m - 1) / m;   // check degrees at most ceil(E/m)
+    d.pwide = rows_cap(prm, n, m);
+    d.pmax = std::min(d.pwide, m);
+    d.eamax = d.pmax * dmax;
+    d.eawide = d.pwide * dmax;
+    Layout L, Lw;
+    if (!make_layouts(d, budget, precision == LPDEC_MIXED ? 4 : 8, precision == LPDEC_M32,
+                      dense_rows_for(d), &L, &Lw))
+        return LPDEC_ERR_INVALID_ARG;
     if (L.smem_bytes == 0xffffffffu) return LPDEC_ERR_INVALID_ARG;
     if (smem_bytes) *smem_bytes = L.smem_bytes + sizeof(KernelShared);
-    if (global_bytes_per_frame) *global_bytes_per_frame = (size_t)L.gbytes;
+    if (global_bytes_per_frame) *global_bytes_per_frame = (size_t)L.stride;
     return LPDEC_OK;
 }
 
@@ -1139,17 +1187,18 @@ int32_t noalloc_launch_plan(const lpdec_params& prm, const lpdec_code* code, int
     // The dense fallback of stalled Newton solves, as in the regular entry,
     // whenever one CTA's workspace with its matrix fits the array; the grid
     // then shrinks to the CTAs the array holds.
-    Layout L = make_layout(d, budget, real_bytes, prm.precision == LPDEC_M32, dense_rows_for(d));
-    if (L.smem_bytes != 0xffffffffu && L.gbytes > avail)
-        L = make_layout(d, budget, real_bytes, prm.precision == LPDEC_M32, 0);
-    if (L.smem_bytes == 0xffffffffu || L.smem_bytes + sizeof(KernelShared) > (size_t)optin) {
+    const bool m32 = prm.precision == LPDEC_M32;
+    Layout L, Lw;
+    bool ok = make_layouts(d, budget, real_bytes, m32, dense_rows_for(d), &L, &Lw);
+    if (ok && L.stride > avail) ok = make_layouts(d, budget, real_bytes, m32, 0, &L, &Lw);
+    if (!ok || L.smem_bytes + sizeof(KernelShared) > (size_t)optin) {
         snprintf(g_err, sizeof g_err, "frame workspace does not fit in shared memory");
         return LPDEC_ERR_INVALID_ARG;
     }
-    if (L.gbytes > avail) {
+    if (L.stride > avail) {
         snprintf(g_err, sizeof g_err,
                  "one frame needs %llu bytes of scratch, above the %zu-byte static array",
-                 (unsigned long long)L.gbytes, avail);
+                 (unsigned long long)L.stride, avail);
         return LPDEC_ERR_OUT_OF_BUDGET;
     }
     CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
@@ -1159,9 +1208,10 @@ int32_t noalloc_launch_plan(const lpdec_params& prm, const lpdec_code* code, int
         snprintf(g_err, sizeof g_err, "kernel does not fit on an SM");
         return LPDEC_ERR_INVALID_ARG;
     }
-    size_t by_scratch = L.gbytes ? avail / L.gbytes : (size_t)per_sm * sms;
+    size_t by_scratch = L.stride ? avail / L.stride : (size_t)per_sm * sms;
     int grid = (int)std::min<size_t>({(size_t)nframes, (size_t)per_sm * sms, by_scratch});
     out->L = L;
+    out->Lw = Lw;
     out->threads = threads;
     out->grid = std::max(1, grid);
     return LPDEC_OK;
@@ -1198,12 +1248,12 @@ extern "C" int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
     CK(cudaMemsetAsync(counter, 0, sizeof(int), s));   // the only state a call must reset
     if (mixed)
         k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            view_of(code, prm), nullptr, nullptr, to_dev(prm), ln.L, d_gamma, d_u, d_hard,
+            view_of(code, prm), nullptr, nullptr, to_dev(prm), ln.L, ln.Lw, d_gamma, d_u, d_hard,
             d_cert, d_cut_mask, d_stats,
             nframes, counter, gscratch);
     else
         k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
-            view_of(code, prm), nullptr, nullptr, to_dev(prm), ln.L, d_gamma, d_u, d_hard,
+            view_of(code, prm), nullptr, nullptr, to_dev(prm), ln.L, ln.Lw, d_gamma, d_u, d_hard,
             d_cert, d_cut_mask, d_stats,
             nframes, counter, gscratch);
     CK(cudaGetLastError());

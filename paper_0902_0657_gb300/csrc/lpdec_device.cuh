@@ -27,11 +27,13 @@ constexpr uint16_t kIdx = 0x7fffu;
 // ---------------------------------------------------------------------------
 // Code (H) view: CSR rows = checks, CSC columns = bits. Read-only, shared by
 // every frame of the code (n, m <= 32767). pmax / eamax: capacity of one
-// frame's LP (rows, and nonzeros of the standard part of A).
+// frame's LP (rows, and nonzeros of the standard part of A) in the main
+// workspace; pwide / eawide: in the wide workspace a frame moves to when its
+// cut list outgrows the main one (ALP holds several rows per check).
 // ---------------------------------------------------------------------------
 struct CodeView {
     int n, m, E;
-    int pmax, eamax;
+    int pmax, eamax, pwide, eawide;
     const int* __restrict__ h_ptr;   // [m+1]
     const int* __restrict__ h_col;   // [E] bit of CSR edge e
     const int* __restrict__ e_chk;   // [E] check of CSR edge e
@@ -44,6 +46,7 @@ struct DevParams {
     double sigma, eta, tol_gap, tol_feas, tol_pcg, tau_act, tau_cut, tau_int;
     double pcg_gap_factor, tol_inner, tol_feas_loose, tol_cert, tau_inc;
     int max_alp, max_ipm, max_pcg, variant, precision;
+    int precond, precond_switch;
 };
 
 // ---------------------------------------------------------------------------
@@ -60,8 +63,8 @@ enum Arr {
     S_DEG, S_BITMAP, S_FLAGS, S_MASK, S_FLIP, S_HPTR, S_VPTR,
     S_BPTR, S_BDEP, S_FPTR, S_FDEP,   // dependency lists of the two triangular solves
     S_VEC,      // PCG vectors of type T: xs, r, z, h, l (pmax each), t (n), d2t (n+pmax),
-                // invd2p (pmax); during the MTS selection the same bytes hold the u64
-                // sort keys [q2] followed by rank [q] and sorted [q] (uint16)
+                // invd2p (pmax); during the MTS selection the same bytes hold the sort keys
+                // (u64 [q2], u32 [q2]) followed by rank [q] and sorted [q] (uint16)
     // FP64 interior-point state (global scratch)
     G_X, G_Z, G_RC, G_D2, G_Y, G_B, G_W, G_DY, G_R64, G_U, G_T64, G_BASIC,
     // optimality certificate scratch: vertex and CG vectors over columns
@@ -96,10 +99,20 @@ struct Layout {
     uint32_t off[A_COUNT];     // byte offset; kGlobalBit set = global scratch
     uint32_t smem_bytes;       // dynamic shared memory per CTA
     uint32_t q2;               // power of two >= nmax + pmax (sort width)
-    uint32_t dense;            // 1 = G_QD holds a pmax x pmax FP64 matrix
+    uint32_t dense;            // rows of the dense fallback's FP64 matrix in G_QD (0: off)
     uint32_t nmax, mmax, pmax; // capacities the arrays are sized for
-    unsigned long long gbytes; // global scratch bytes per CTA
+    unsigned long long gbytes; // global scratch bytes of this workspace per CTA
+    unsigned long long stride; // global scratch bytes per CTA (main + wide workspace)
 };
+
+// Arrays whose size depends on the LP's row capacity; a frame moved to the
+// wide workspace takes these from it and keeps the others (per check, per
+// bit, the code's pointers, the dense fallback's matrix) where they were.
+__host__ __device__ constexpr bool row_sized(int a) {
+    return !(a == S_FLAGS || a == S_MASK || a == S_FLIP || a == S_HPTR || a == S_VPTR ||
+             a == S_CPTR || a == S_CRPTR || a == G_U || a == G_T64 || a == G_QD ||
+             a == G_CRPTR2);
+}
 
 template <typename T>
 struct WS {
@@ -114,6 +127,7 @@ struct WS {
     T *xs, *r, *z, *h, *l, *t, *d2t, *invd2p;
     float *rf, *zf, *ip32;      // FP32 M-solve vectors (LPDEC_M32 only)
     unsigned long long* skey;   // aliases the PCG vectors
+    uint32_t* sidx;             // column index of each sort key
     double *x, *zz, *rc, *d2, *y, *b, *w, *dy, *r64, *u, *t64;
     double *vx, *v1, *v2, *v3, *v4, *vr1, *vr2, *p64;
     double* qd;   // dense Cholesky factor (column-major p x p), null when off
@@ -129,12 +143,14 @@ __device__ __forceinline__ char* ws_ptr(const Layout& L, int a, char* smem, char
 }
 
 // Pointers of one CTA's workspace; sub-arrays of S_VEC and G_P64 are sliced
-// with the layout's capacities, so frames of any smaller code fit.
+// with the layout's capacities, so frames of any smaller code fit. With
+// only_rows, only the row-sized arrays are (re)pointed (moving a frame to the
+// wide workspace).
 template <typename T>
-__device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws) {
+__device__ inline void point_ws(WS<T>& w, const Layout& L, char* smem, char* gws, bool only_rows) {
     const int n = (int)L.nmax, pm = (int)L.pmax;
-    WS<T> w;
-#define P_(Ty, name, id) w.name = reinterpret_cast<Ty*>(ws_ptr(L, id, smem, gws))
+#define P_(Ty, name, id) \
+    if (!only_rows || row_sized(id)) w.name = reinterpret_cast<Ty*>(ws_ptr(L, id, smem, gws))
     P_(uint16_t, rowent, S_ROWENT); P_(uint16_t, colent, S_COLENT);
     P_(uint16_t, cchk, S_CCHK); P_(uint32_t, cmask, S_CMASK); P_(uint8_t, cact, S_CACT);
     P_(uint32_t, rptr, S_RPTR); P_(uint32_t, cptr, S_CPTR); P_(uint32_t, crptr, S_CRPTR);
@@ -151,7 +167,8 @@ __device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws) {
     P_(uint16_t, bdep, S_BDEP); P_(uint16_t, fdep, S_FDEP);
     T* v = reinterpret_cast<T*>(ws_ptr(L, S_VEC, smem, gws));
     w.skey = reinterpret_cast<unsigned long long*>(v);
-    w.rank = reinterpret_cast<uint16_t*>(w.skey + L.q2);
+    w.sidx = reinterpret_cast<uint32_t*>(w.skey + L.q2);
+    w.rank = reinterpret_cast<uint16_t*>(w.sidx + L.q2);
     w.sorted = w.rank + (n + pm);
     w.xs = v; v += pm; w.r = v; v += pm; w.z = v; v += pm; w.h = v; v += pm; w.l = v; v += pm;
     w.t = v; v += n; w.d2t = v; v += n + pm; w.invd2p = v;
@@ -166,11 +183,19 @@ __device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws) {
     P_(double, qd, G_QD);
     P_(uint16_t, cchk2, G_CCHK2); P_(uint32_t, cmask2, G_CMASK2);
     P_(uint32_t, crptr2, G_CRPTR2);
-    if (!L.dense) w.qd = nullptr;
-    w.dense_p = (int)L.dense;
+#undef P_
+    if (!only_rows) {
+        if (!L.dense) w.qd = nullptr;
+        w.dense_p = (int)L.dense;
+    }
     w.cap_n = n;
     w.cap_p = pm;
-#undef P_
+}
+
+template <typename T>
+__device__ inline WS<T> make_ws(const Layout& L, char* smem, char* gws) {
+    WS<T> w;
+    point_ws<T>(w, L, smem, gws, false);
     return w;
 }
 
@@ -198,6 +223,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W) {
     v.rf = W.rf; v.zf = W.zf; v.ip32 = W.ip32;
     v.d2t = W.d2;
     v.skey = nullptr;
+    v.sidx = nullptr;
     v.x = W.x; v.zz = W.zz; v.rc = W.rc; v.d2 = W.d2; v.y = W.y; v.b = W.b; v.w = W.w;
     v.dy = W.dy; v.r64 = W.r64; v.u = W.u; v.t64 = W.t64;
     v.vx = W.vx; v.v1 = W.v1; v.v2 = W.v2; v.v3 = W.v3; v.v4 = W.v4; v.vr1 = W.vr1;
@@ -386,11 +412,11 @@ __device__ inline void drop_inactive(Blk& B, const CodeView& C, WS<T>& W) {
 // Packed entries: rowent[rptr[r] + t] = bit | sign of the t-th neighbour of
 // the row's check; colent[cptr[i] ..] = (row | sign) over the rows that hold
 // bit i, in increasing row order. Returns false (LP left unchanged) when the
-// new list exceeds the frame's capacity (C.pmax rows, C.eamax entries).
+// new list exceeds the workspace's capacity (pcap rows, eacap entries).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ inline bool lp_build(Blk& B, const CodeView& C, WS<T>& W, Frame& F, int* shscan,
-                                bool alp) {
+                                bool alp, int pcap, int eacap) {
     // 1. new cut list, grouped by check
     int per = (C.m + B.nt - 1) / B.nt;
     int j0 = B.tid * per, j1 = min(C.m, j0 + per);
@@ -405,7 +431,7 @@ __device__ inline bool lp_build(Blk& B, const CodeView& C, WS<T>& W, Frame& F, i
     int p, ne_all;
     int pos = bscan_excl(B, cnt, &p, shscan);
     bscan_excl(B, cne, &ne_all, shscan);
-    if (p > C.pmax || ne_all > C.eamax) return false;   // same decision in every thread
+    if (p > pcap || ne_all > eacap) return false;   // same decision in every thread
     // (the old list is only read until the barrier; the new one goes to the
     // G_*2 arrays first)
     for (int j = j0; j < j1; ++j) {
@@ -515,19 +541,15 @@ __device__ __forceinline__ V rowA(const CodeView& C, const WS<T>& W, int r, cons
 // ---------------------------------------------------------------------------
 // a4: column-wise greedy MTS (Algorithm 7) with weights wt[0..q).
 // Columns are ranked once by (weight desc, index asc) with a bitonic sort on
-// the weights rounded to FP32; DEG1 is a bitmap over ranks, so "maximum-
-// weight degree-1 column" is the first set bit. One warp runs the p greedy
-// steps: lanes scan the bitmap and update the columns of the removed row.
-// The forward-solve level of each row is fixed when its pivot is chosen and
-// the back-substitution levels follow in reverse selection order.
+// the FP64 weights; DEG1 is a bitmap over ranks, so "maximum-weight
+// degree-1 column" is the first set bit. One warp runs the p greedy steps:
+// lanes scan the bitmap and update the columns of the removed row. The
+// forward-solve level of each row is fixed when its pivot is chosen and the
+// back-substitution levels follow in reverse selection order.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t desc_key32(float v) {
-    uint32_t b = __float_as_uint(v);
-    uint32_t asc = (b >> 31) ? ~b : (b | 0x80000000u);
-    return ~asc;
-}
 
-__device__ inline void bitonic_sort(Blk& B, unsigned long long* key, int n2) {
+// Bitonic sort of n2 (a power of two) composite keys (key, idx), ascending.
+__device__ inline void bitonic_sort(Blk& B, unsigned long long* key, uint32_t* idx, int n2) {
     for (int k = 2; k <= n2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int t = B.tid; t < (n2 >> 1); t += B.nt) {
@@ -535,7 +557,9 @@ __device__ inline void bitonic_sort(Blk& B, unsigned long long* key, int n2) {
                 int l = i + j;
                 bool up = (i & k) == 0;
                 unsigned long long ki = key[i], kl = key[l];
-                if ((ki > kl) == up) { key[i] = kl; key[l] = ki; }
+                uint32_t ii = idx[i], il = idx[l];
+                bool gt = ki > kl || (ki == kl && ii > il);
+                if (gt == up) { key[i] = kl; key[l] = ki; idx[i] = il; idx[l] = ii; }
             }
             __syncthreads();
         }
@@ -588,11 +612,49 @@ __device__ inline void build_deps(Blk& B, const CodeView& C, WS<T>& W, const Fra
     __syncthreads();
 }
 
-// Level buckets (counting sort) of both solves from lb / lf, pivot signs,
-// and the dependency lists. Shared by every MTS selection.
+// Levels of both solves from the dependency lists, on warp B.sw, for a
+// lower-triangular selection order selrow[0..p) (Algorithms 5, 6, 8): a row's
+// back-substitution step needs rows pivoting earlier columns (levels in
+// selection order), its forward step needs the later rows of its pivot
+// column (levels in reverse order).
 template <typename T>
-__device__ inline Levels finish_levels(Blk& B, const CodeView& C, WS<T>& W, const Frame& F) {
+__device__ inline void levels_from_deps(Blk& B, WS<T>& W, int p) {
+    if (B.warp == B.sw) {
+        for (int k = 0; k < p; ++k) {
+            const int r = W.selrow[k];
+            int lv = 0;
+            for (uint32_t t = W.bptr[r] + B.lane; t < W.bptr[r + 1]; t += 32)
+                lv = max(lv, (int)W.lb[W.bdep[t] & kIdx]);
+            lv = (int)__reduce_max_sync(kFull, (unsigned)lv) + 1;
+            if (B.lane == 0) W.lb[r] = (uint16_t)lv;
+            __syncwarp();
+        }
+        for (int k = p - 1; k >= 0; --k) {
+            const int r = W.selrow[k];
+            int lv = 0;
+            for (uint32_t t = W.fptr[r] + B.lane; t < W.fptr[r + 1]; t += 32)
+                lv = max(lv, (int)W.lf[W.fdep[t] & kIdx]);
+            lv = (int)__reduce_max_sync(kFull, (unsigned)lv) + 1;
+            if (B.lane == 0) W.lf[r] = (uint16_t)lv;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+// Dependency lists, then (lower = true: from them, else already set by the
+// selection) the levels of both solves, their buckets (counting sort) and
+// the pivot signs. Shared by every MTS selection.
+template <typename T>
+__device__ inline Levels finish_levels(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                                       bool lower = false) {
     const int n = C.n, p = F.p;
+    build_deps<T>(B, C, W, F);
+    if (lower) {
+        for (int r = B.tid; r < p; r += B.nt) { W.lb[r] = 0; W.lf[r] = 0; }
+        __syncthreads();
+        levels_from_deps<T>(B, W, p);
+    }
     int mb = 0, mf = 0;
     for (int r = B.tid; r < p; r += B.nt) {
         mb = max(mb, (int)W.lb[r]);
@@ -636,7 +698,6 @@ __device__ inline Levels finish_levels(Blk& B, const CodeView& C, WS<T>& W, cons
     __syncthreads();
     for (int r = B.tid; r < p; r += B.nt) W.lfrows[atomicAdd(&W.cur[W.lf[r]], 1u)] = (uint16_t)r;
     __syncthreads();
-    build_deps<T>(B, C, W, F);
     return L;
 }
 
@@ -646,13 +707,16 @@ __device__ inline void rank_columns(Blk& B, WS<T>& W, const Frame& F, const doub
     const int q = F.q;
     int q2 = 1;
     while (q2 < q) q2 <<= 1;
-    for (int k = B.tid; k < q2; k += B.nt)
-        W.skey[k] = (k < q) ? (((unsigned long long)desc_key32((float)wt[k]) << 32) | (unsigned)k)
-                            : ~0ull;
+    // positive doubles order as their bit patterns; the complement makes the
+    // ascending sort put the largest weight first (padding sorts last)
+    for (int k = B.tid; k < q2; k += B.nt) {
+        W.skey[k] = (k < q) ? ~(unsigned long long)__double_as_longlong(wt[k]) : ~0ull;
+        W.sidx[k] = (uint32_t)k;
+    }
     __syncthreads();
-    bitonic_sort(B, W.skey, q2);
+    bitonic_sort(B, W.skey, W.sidx, q2);
     for (int k = B.tid; k < q; k += B.nt) {
-        int i = (int)(W.skey[k] & 0xffffffffu);
+        int i = (int)W.sidx[k];
         W.rank[i] = (uint16_t)k;
         W.sorted[k] = (uint16_t)i;
     }
@@ -754,6 +818,321 @@ __device__ inline Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const F
     }
     __syncthreads();
     return finish_levels<T>(B, C, W, F);
+}
+
+// Rows of column c of the LP (its LP rows through colent; a slack column's
+// only row), for warp loops: count and t-th row.
+template <typename T>
+__device__ __forceinline__ int col_nrows(const WS<T>& W, int n, int c) {
+    return c < n ? (int)(W.cptr[c + 1] - W.cptr[c]) : 1;
+}
+template <typename T>
+__device__ __forceinline__ int col_row(const WS<T>& W, int n, int c, int t) {
+    return c < n ? (int)(W.colent[W.cptr[c] + t] & kIdx) : c - n;
+}
+
+// Lowest set bit of a bitmap of nw words, over the warp (~0u if none).
+__device__ __forceinline__ unsigned warp_first_bit(const uint32_t* bm, int nw, int lane) {
+    unsigned best = 0xffffffffu;
+    for (int wd = lane; wd < nw; wd += 32) {
+        uint32_t v = bm[wd];
+        if (v) { best = (unsigned)(wd * 32 + __ffs(v) - 1); break; }
+    }
+    return __reduce_min_sync(kFull, best);
+}
+
+__device__ __forceinline__ void bit_set(uint32_t* bm, int i) { atomicOr(&bm[i >> 5], 1u << (i & 31)); }
+__device__ __forceinline__ void bit_clear(uint32_t* bm, int i) { atomicAnd(&bm[i >> 5], ~(1u << (i & 31))); }
+
+// ---------------------------------------------------------------------------
+// a4 (variant): row-wise greedy MTS with diagonal expansion (Algorithm 8),
+// on warp B.sw. While a column is left: if some row has exactly one live
+// column, the lowest such row pivots it and the column is removed;
+// otherwise the live column of least weight (ties: lowest index) is removed.
+// Rows never pivoted then take their own slack columns in increasing order.
+// The order is lower triangular. rowdeg lives in lb until the levels are
+// computed.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline Levels mts_rowwise(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                                     const double* wt) {
+    const int n = C.n, p = F.p, q = F.q;
+    uint16_t* rowdeg = W.lb;
+    for (int i = B.tid; i < q; i += B.nt) {
+        W.deg[i] = (uint16_t)(col_nrows(W, n, i) > 0 ? 1 : 0);   // live
+        W.pivrow[i] = kNone;
+    }
+    for (int r = B.tid; r < p; r += B.nt) {
+        W.pivcol[r] = kNone;
+        rowdeg[r] = (uint16_t)(W.rptr[r + 1] - W.rptr[r] + 1);
+    }
+    rank_columns<T>(B, W, F, wt);   // (barriers inside)
+    const int nwr = (p + 31) / 32;
+    for (int k = B.tid; k < nwr; k += B.nt) W.bitmap[k] = 0;   // rows of degree 1 (none yet)
+    __syncthreads();
+    if (B.warp == B.sw) {
+        const int lane = B.lane;
+        int live = 0;
+        for (int i = lane; i < q; i += 32) live += W.deg[i];
+        for (int o = 16; o > 0; o >>= 1) live += __shfl_xor_sync(kFull, live, o);
+        int k = 0, lo = q - 1;
+        while (live > 0) {
+            const unsigned j = warp_first_bit(W.bitmap, nwr, lane);
+            int victim;
+            if (j < (unsigned)p) {
+                const int e0 = (int)W.rptr[j], d = (int)W.rptr[j + 1] - e0;
+                unsigned cand = 0xffffffffu;
+                for (int t = lane; t <= d; t += 32) {
+                    int c = (t < d) ? (W.rowent[e0 + t] & kIdx) : n + (int)j;
+                    if (W.deg[c]) cand = min(cand, (unsigned)c);
+                }
+                victim = (int)__reduce_min_sync(kFull, cand);
+                if (lane == 0) {
+                    W.pivcol[j] = (uint16_t)victim;
+                    W.pivrow[victim] = (uint16_t)j;
+                    W.selrow[k] = (uint16_t)j;
+                }
+                ++k;
+            } else {
+                // least weight, then lowest index: the first live entry of
+                // the run of equal weights that ends at the last live entry
+                while (lo >= 0 && !W.deg[W.sorted[lo]]) --lo;
+                int t = lo;
+                const double wl = wt[W.sorted[lo]];
+                while (t > 0 && wt[W.sorted[t - 1]] == wl) --t;
+                while (!W.deg[W.sorted[t]]) ++t;
+                victim = W.sorted[t];
+            }
+            __syncwarp();
+            if (lane == 0) W.deg[victim] = 0;
+            const int nr = col_nrows(W, n, victim);
+            for (int t = lane; t < nr; t += 32) {
+                const int r = col_row(W, n, victim, t);
+                const int nd = (int)rowdeg[r] - 1;
+                rowdeg[r] = (uint16_t)nd;
+                if (nd == 1) bit_set(W.bitmap, r);
+                else if (nd == 0) bit_clear(W.bitmap, r);
+            }
+            --live;
+            __syncwarp();
+        }
+        // diagonal expansion
+        for (int base = 0; base < p; base += 32) {
+            const int j = base + lane;
+            const bool need = j < p && W.pivcol[j] == kNone;
+            const unsigned bal = __ballot_sync(kFull, need);
+            if (need) {
+                const int pos = k + __popc(bal & ((1u << lane) - 1u));
+                W.pivcol[j] = (uint16_t)(n + j);
+                W.pivrow[n + j] = (uint16_t)j;
+                W.selrow[pos] = (uint16_t)j;
+            }
+            k += __popc(bal);
+        }
+    }
+    __syncthreads();
+    return finish_levels<T>(B, C, W, F, true);
+}
+
+// ---------------------------------------------------------------------------
+// a4 (variant): incremental greedy MTS (Algorithm 6) with the triangulation
+// step (Algorithm 5), on warp B.sw. Columns are scanned by decreasing weight
+// (ties: lower index) and kept when the set stays triangular, until p are
+// kept. Whether S + {c} can be made lower triangular is decided exactly:
+//   - if a row of c holds no column of S, c can come first (it pivots that
+//     row; rows holding c only gain an earlier column): kept;
+//   - if no row of c is the pivot row of a column of S (under the current
+//     assignment of pivot rows), c can come last, pivoting its lowest row:
+//     kept;
+//   - otherwise by peeling S + {c} (Algorithm 5: a row with exactly one live
+//     column pivots it; the set is triangular iff every column peels), whose
+//     pivots become the new assignment when it succeeds.
+// The final (column, row) pairs and order are those of Algorithm 5 on the
+// kept set with the lowest-index degree-1 row taken at each step. Scratch:
+// rowcnt (S columns per row) in lb, live-row counts in lf, live stamps in
+// rank, the set S in lbrows, the peel's rows / columns in lfrows / cchk2, a
+// stack of degree-1 rows in selrow.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ inline int peel_set(Blk& B, WS<T>& W, int n, int p, int s, uint16_t stamp,
+                               bool lowest_first) {
+    // live columns (S, stamped) of every row; degree-1 rows on a stack (or,
+    // for the lowest-first order, in the bitmap)
+    const int lane = B.lane;
+    uint16_t* cnt = W.lf;
+    uint16_t* stk = W.selrow;
+    int top = 0;
+    const int nwr = (p + 31) / 32;
+    if (lowest_first)
+        for (int k = lane; k < nwr; k += 32) W.bitmap[k] = 0;
+    __syncwarp();
+    for (int base = 0; base < p; base += 32) {
+        const int r = base + lane;
+        int c = 0;
+        if (r < p) {
+            for (uint32_t e = W.rptr[r]; e < W.rptr[r + 1]; ++e)
+                c += W.rank[W.rowent[e] & kIdx] == stamp;
+            c += W.rank[n + r] == stamp;
+            cnt[r] = (uint16_t)c;
+        }
+        const unsigned bal = __ballot_sync(kFull, r < p && c == 1);
+        if (r < p && c == 1) {
+            if (lowest_first) bit_set(W.bitmap, r);
+            else stk[top + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)r;
+        }
+        top += __popc(bal);
+    }
+    __syncwarp();
+    int peeled = 0;
+    for (;;) {
+        int j;
+        if (lowest_first) {
+            const unsigned b = warp_first_bit(W.bitmap, nwr, lane);
+            if (b >= (unsigned)p) break;
+            j = (int)b;
+        } else {
+            if (top == 0) break;
+            j = stk[--top];
+            if (cnt[j] != 1) continue;   // (uniform: every lane reads the same)
+        }
+        const int e0 = (int)W.rptr[j], d = (int)W.rptr[j + 1] - e0;
+        unsigned cand = 0xffffffffu;
+        for (int t = lane; t <= d; t += 32) {
+            int c = (t < d) ? (W.rowent[e0 + t] & kIdx) : n + j;
+            if (W.rank[c] == stamp) cand = min(cand, (unsigned)c);
+        }
+        const int x = (int)__reduce_min_sync(kFull, cand);
+        __syncwarp();
+        if (lane == 0) {
+            W.rank[x] = 0;
+            W.lfrows[peeled] = (uint16_t)j;
+            W.cchk2[peeled] = (uint16_t)x;
+        }
+        ++peeled;
+        const int nr = col_nrows(W, n, x);
+        for (int base = 0; base < nr; base += 32) {   // uniform trip count
+            const int t = base + lane;
+            int pr = -1;
+            if (t < nr) {
+                const int r = col_row(W, n, x, t);
+                const int nd = (int)cnt[r] - 1;
+                cnt[r] = (uint16_t)nd;
+                if (lowest_first) {
+                    if (nd == 1) bit_set(W.bitmap, r);
+                    else if (nd == 0) bit_clear(W.bitmap, r);
+                } else if (nd == 1) {
+                    pr = r;
+                }
+            }
+            if (!lowest_first) {
+                const unsigned bal = __ballot_sync(kFull, pr >= 0);
+                if (pr >= 0) stk[top + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)pr;
+                top += __popc(bal);
+            }
+        }
+        __syncwarp();
+    }
+    (void)s;
+    return peeled;
+}
+
+template <typename T>
+__device__ inline Levels mts_incremental(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                                         const double* wt) {
+    const int n = C.n, p = F.p, q = F.q;
+    uint16_t* rowcnt = W.lb;
+    for (int i = B.tid; i < q; i += B.nt) { W.pivrow[i] = kNone; W.deg[i] = 0; }
+    for (int r = B.tid; r < p; r += B.nt) { W.pivcol[r] = kNone; rowcnt[r] = 0; }
+    rank_columns<T>(B, W, F, wt);   // (barriers inside)
+    for (int i = B.tid; i < q; i += B.nt) W.rank[i] = 0;   // live stamps from here on
+    __syncthreads();
+    if (B.warp == B.sw) {
+        const int lane = B.lane;
+        int s = 0;
+        uint16_t stamp = 0;
+        for (int k = 0; k < q && s < p; ++k) {
+            const int c = W.sorted[k];
+            const int nr = col_nrows(W, n, c);
+            if (nr == 0) continue;                 // a zero column is never triangular
+            unsigned empty = 0xffffffffu, any = 0xffffffffu;
+            int piv = 0;
+            for (int t = lane; t < nr; t += 32) {
+                const int r = col_row(W, n, c, t);
+                if (rowcnt[r] == 0) empty = min(empty, (unsigned)r);
+                any = min(any, (unsigned)r);
+                piv |= W.pivcol[r] != kNone;
+            }
+            empty = __reduce_min_sync(kFull, empty);
+            any = __reduce_min_sync(kFull, any);
+            piv = __any_sync(kFull, piv);
+            bool keep = false;
+            if (empty < (unsigned)p || !piv) {
+                const int r0 = (int)(empty < (unsigned)p ? empty : any);
+                __syncwarp();
+                if (lane == 0) { W.pivcol[r0] = (uint16_t)c; W.pivrow[c] = (uint16_t)r0; }
+                keep = true;
+            } else {
+                // Algorithm 5 on S + {c}
+                if (++stamp == 0) {            // (never with q < 65535 candidates)
+                    for (int i = lane; i < q; i += 32) W.rank[i] = 0;
+                    stamp = 1;
+                }
+                __syncwarp();
+                for (int t = lane; t < s; t += 32) W.rank[W.lbrows[t]] = stamp;
+                if (lane == 0) W.rank[c] = stamp;
+                __syncwarp();
+                const int peeled = peel_set<T>(B, W, n, p, s + 1, stamp, false);
+                if (peeled == s + 1) {
+                    for (int r = lane; r < p; r += 32) W.pivcol[r] = kNone;
+                    __syncwarp();
+                    for (int t = lane; t < peeled; t += 32) {
+                        const int j = W.lfrows[t], x = W.cchk2[t];
+                        W.pivcol[j] = (uint16_t)x;
+                        W.pivrow[x] = (uint16_t)j;
+                    }
+                    keep = true;
+                }
+            }
+            if (keep) {
+                for (int t = lane; t < nr; t += 32) {
+                    const int r = col_row(W, n, c, t);
+                    rowcnt[r] = (uint16_t)(rowcnt[r] + 1);
+                }
+                if (lane == 0) { W.lbrows[s] = (uint16_t)c; W.deg[c] = 1; }
+                ++s;
+            }
+            __syncwarp();
+        }
+        // final pairs and order: Algorithm 5 on the kept set, lowest-index
+        // degree-1 row first
+        if (++stamp == 0) {
+            for (int i = lane; i < q; i += 32) W.rank[i] = 0;
+            stamp = 1;
+        }
+        __syncwarp();
+        for (int t = lane; t < s; t += 32) W.rank[W.lbrows[t]] = stamp;
+        for (int r = lane; r < p; r += 32) W.pivcol[r] = kNone;
+        __syncwarp();
+        const int peeled = peel_set<T>(B, W, n, p, s, stamp, true);
+        for (int t = lane; t < peeled; t += 32) {
+            const int j = W.lfrows[t], x = W.cchk2[t];
+            W.pivcol[j] = (uint16_t)x;
+            W.pivrow[x] = (uint16_t)j;
+            W.selrow[t] = (uint16_t)j;
+        }
+    }
+    __syncthreads();
+    return finish_levels<T>(B, C, W, F, true);
+}
+
+// The preconditioner of one Newton system: Algorithm 7 (column-wise), 6
+// (incremental) or 8 (row-wise).
+template <typename T>
+__device__ inline Levels select_mts(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                                    const double* wt, int kind) {
+    if (kind == LPDEC_MTS_INCREMENTAL) return mts_incremental<T>(B, C, W, F, wt);
+    if (kind == LPDEC_MTS_ROWWISE) return mts_rowwise<T>(B, C, W, F, wt);
+    return mts_select<T>(B, C, W, F, wt, 0);
 }
 
 // Selection order as (column, row) pairs, for the step entry point.
@@ -1525,6 +1904,9 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
     F.normc = sqrt(bsum(B, nc2));   // (barrier inside)
     bool force64 = false, force_dense = false;
     int last_pcg = 0;
+    // preconditioner of this LP's Newton systems (LPDEC_MTS_ADAPTIVE starts
+    // column-wise and turns incremental for good after a long PCG run)
+    int kind = P.precond == LPDEC_MTS_ADAPTIVE ? LPDEC_MTS_COLUMN : P.precond;
     double prev_grel = INFINITY, sig0 = -1.0, sig1 = -1.0;
     for (int it = 0;; ++it) {
         // Expensive regime (the basis certificate keeps failing and Newton
@@ -1591,7 +1973,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
         // w = r_b + A D^2 r_c - A Z^-1 r_e (Eq. 24 right side)
         for (int r = B.tid; r < p; r += B.nt) W.w[r] += rowA<double>(C, W, r, W.rc) + W.rc[n + r];
         __syncthreads();
-        Levels L = mts_select<T>(B, C, W, F, W.d2, q2);
+        Levels L = select_mts<T>(B, C, W, F, W.d2, kind);
         o.max_levels = max(o.max_levels, max(L.nb, L.nf));
         // near the optimum the selected basis may already be optimal
         if (g_rel < P.tol_cert && certify_basis<T>(B, C, W, F, L, gamma)) {
@@ -1615,6 +1997,8 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
         o.flops += no.flops;
         o.bytes += no.bytes;
         last_pcg = no.dense ? 1000000 : no.iters;
+        if (P.precond == LPDEC_MTS_ADAPTIVE && (no.dense || no.iters > P.precond_switch))
+            kind = LPDEC_MTS_INCREMENTAL;
         if (no.relres > 1e-3 && g_rel < 1e-6) {   // no usable direction left near the optimum
             o.iters = it;
             break;
@@ -1800,9 +2184,24 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// Moves a frame's cut list to the wide workspace (Lw, at gw): the row-sized
+// arrays are re-pointed there, the list itself (rows and masks) copied.
 template <typename T>
-__device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const DevParams& P,
-                                    const double* gamma, FrameOut out, int q2, int* shscan) {
+__device__ inline void widen(Blk& B, WS<T>& W, const Layout& Lw, char* gw, int p) {
+    uint16_t* cchk = W.cchk;
+    uint32_t* cmask = W.cmask;
+    point_ws<T>(W, Lw, nullptr, gw, true);
+    for (int r = B.tid; r < p; r += B.nt) { W.cchk[r] = cchk[r]; W.cmask[r] = cmask[r]; }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ inline void decode_frame(Blk& B, const CodeView& C, const WS<T>& W0,
+                                    const DevParams& P, const double* gamma, FrameOut out,
+                                    int q2, int* shscan, const Layout* Lw = nullptr,
+                                    char* gw = nullptr) {
+    WS<T> W = W0;   // (the wide workspace, if this frame moves there, is its own)
+    bool wide = false;
     const unsigned long long t0 = global_ns();
     int bad = 0;
     for (int i = B.tid; i < C.n; i += B.nt) bad |= !isfinite(gamma[i]);
@@ -1831,7 +2230,14 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, WS<T>& W, const D
         int added = cut_search<T>(B, C, W, P, alp);
         if (!added) break;
         if (st.alp_iters >= P.max_alp) { status = LPDEC_ERR_NOT_CONVERGED; break; }
-        if (!lp_build<T>(B, C, W, F, shscan, alp)) { status = LPDEC_ERR_OUT_OF_BUDGET; break; }
+        bool built = lp_build<T>(B, C, W, F, shscan, alp, wide ? C.pwide : C.pmax,
+                                 wide ? C.eawide : C.eamax);
+        if (!built && !wide && Lw && C.pwide > C.pmax) {
+            widen<T>(B, W, *Lw, gw, F.p);
+            wide = true;
+            built = lp_build<T>(B, C, W, F, shscan, alp, C.pwide, C.eawide);
+        }
+        if (!built) { status = LPDEC_ERR_OUT_OF_BUDGET; break; }
         IpmOut io = ipm_solve<T>(B, C, W, F, P, gamma, q2);
         st.alp_iters++;
         st.ipm_iters_total += io.iters;

@@ -27,6 +27,10 @@ LPDEC_ERR_NO_DEVICE = -7
 LPDEC_MALP_A = 0
 LPDEC_MALP_B = 1
 LPDEC_ALP = 2
+LPDEC_MTS_COLUMN = 0
+LPDEC_MTS_INCREMENTAL = 1
+LPDEC_MTS_ROWWISE = 2
+LPDEC_MTS_ADAPTIVE = 3
 LPDEC_FP64 = 0
 LPDEC_MIXED = 1
 LPDEC_M32 = 2
@@ -38,8 +42,8 @@ class lpdec_params(ctypes.Structure):
                  "pcg_gap_factor", "tol_inner", "tol_feas_loose", "tol_cert", "tau_inc")] + \
                [(k, ctypes.c_int32) for k in
                 ("max_alp", "max_ipm", "max_pcg", "variant", "precision",
-                 "threads_per_block", "smem_budget", "lp_rows_cap")] + \
-               [("reserved", ctypes.c_int32 * 3)]
+                 "threads_per_block", "smem_budget", "lp_rows_cap", "precond",
+                 "precond_switch", "reserved")]
 
 
 class lpdec_stats(ctypes.Structure):

@@ -58,8 +58,7 @@ def test_workspace_layouts_validate(lib, name, precision, budget):
     assert rc == 0 and smem > 0 and glob > 0
     if budget:
         # the always-shared arrays (bitmap, level pointers) may exceed a tiny budget
-        pm = c.m + (c.m + 7) // 8
-        must = 4 * ((c.n + pm + 31) // 32) + 3 * 4 * (pm + 2) + 2048
+        must = 4 * ((c.n + c.m + 31) // 32) + 3 * 4 * (c.m + 2) + 2048
         assert smem <= max(budget, must) + 2048
 
 
@@ -82,7 +81,7 @@ def test_workspace_rejects_bad_sizes(lib):
     c = named_code("peg_1008")
     s64 = L.lpdec_workspace_bytes(c.m, c.n, c.E, L.LPDEC_FP64, 0)[1]
     s32 = L.lpdec_workspace_bytes(c.m, c.n, c.E, L.LPDEC_M32, 0)[1]
-    assert abs(s32 - s64 - 12 * (c.m + (c.m + 7) // 8)) < 16   # three FP32 vectors over the row capacity
+    assert s32 - s64 == 12 * c.m   # three FP32 vectors over the main row capacity (m)
 
 
 def test_no_device_is_reported_not_emulated(lib):
@@ -128,11 +127,11 @@ def test_server_reports_missing_device_and_null_handles(lib):
 
 
 def test_largest_decodable_sizes(lib):
-    """The always-shared arrays (~12 B per LP row of capacity, m + m/8 rows,
-    plus 1 bit per column) bound the decodable size: a 16000 x 32767 code
-    fits one CTA's 227 KB of shared memory, a 32767 x 32767 one does not
-    (its decode calls are rejected)."""
+    """The always-shared arrays (~12 B per LP row of the main workspace, m
+    rows, plus 1 bit per column) bound the decodable size: a 16383 x 32767
+    code fits one CTA's 227 KB of shared memory, a 32767 x 32767 one does
+    not (its decode calls are rejected)."""
     cap = 227 * 1024
-    assert L.lpdec_workspace_bytes(16000, 32767, 3 * 32767, 0, 0)[1] <= cap
+    assert L.lpdec_workspace_bytes(16383, 32767, 3 * 32767, 0, 0)[1] <= cap
     assert L.lpdec_workspace_bytes(32767, 32767, 3 * 32767, 0, 0)[1] > cap
     assert L.lpdec_workspace_bytes(1, 1, 1, 0, 0)[0] == 0          # smallest code

@@ -30,19 +30,26 @@ def compare_frame(res, u, hard, cert, masks, st, ctx=""):
     assert abs(st["objective"] - res.objective) <= 1e-6 * (1 + abs(res.objective)), ctx
 
 
-@pytest.mark.parametrize("precision,threads", [(L.LPDEC_FP64, 128), (L.LPDEC_MIXED, 128),
-                                               (L.LPDEC_M32, 128), (L.LPDEC_FP64, 32),
-                                               (L.LPDEC_MIXED, 256), (L.LPDEC_M32, 64)])
-def test_decode_gallager120_200_frames(precision, threads):
+@pytest.mark.parametrize("precision,threads,precond", [
+    (L.LPDEC_FP64, 128, L.LPDEC_MTS_COLUMN), (L.LPDEC_MIXED, 128, L.LPDEC_MTS_COLUMN),
+    (L.LPDEC_M32, 128, L.LPDEC_MTS_COLUMN), (L.LPDEC_FP64, 32, L.LPDEC_MTS_COLUMN),
+    (L.LPDEC_MIXED, 256, L.LPDEC_MTS_COLUMN), (L.LPDEC_M32, 64, L.LPDEC_MTS_COLUMN),
+    (L.LPDEC_FP64, 128, L.LPDEC_MTS_INCREMENTAL), (L.LPDEC_FP64, 128, L.LPDEC_MTS_ROWWISE),
+    (L.LPDEC_FP64, 128, L.LPDEC_MTS_ADAPTIVE)])
+def test_decode_gallager120_200_frames(precision, threads, precond):
     """(3,6) n=120, Eb/N0 2.0 dB, 200 frames from seed 0, in FP64, in mixed
     precision (FP32 PCG refined against FP64 residuals) and with the FP32
-    preconditioner solve, at several CTA sizes."""
+    preconditioner solve, at several CTA sizes, and with each of the
+    triangular-set preconditioners of Section V (they change the PCG
+    iterations, not the LP solutions)."""
     torch_cuda()
     code = named_code("gallager_120")
     G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(200))
     prm = L.lpdec_default_params()
     prm.precision = precision
     prm.threads_per_block = threads
+    prm.precond = precond
+    prm.precond_switch = 20   # (n = 120: switch early enough to be exercised)
     with L.Decoder(code, params=prm) as d:
         u, hard, cert, masks, st = d.decode_batch(G)
     n_frac = 0

@@ -59,6 +59,7 @@ def test_full_size_matches_oracle_goldens(precision):
     prm = L.lpdec_default_params()
     prm.precision = precision
     worst_u = 0.0
+    failures = []
     with L.Decoder(code, params=prm) as d:
         for eb in sorted({r["ebn0"] for r in rows}):
             grp = [r for r in rows if r["ebn0"] == eb]
@@ -75,17 +76,26 @@ def test_full_size_matches_oracle_goldens(precision):
             u, h, c = host(d_u), host(d_h), host(d_c)
             mk, st = host(d_m).view(np.uint32), host(d_s).view(L.STATS_DTYPE)
             for k, r in enumerate(grp):
-                ctx = (precision, eb, r["frame"])
-                assert st["status"][k] == r["status"], ctx
-                assert np.array_equal(h[k], r["hard_v"]), ctx
-                assert c[k] == r["cert"], ctx
-                assert np.array_equal(mk[k], r["masks_v"]), ctx
-                assert st["alp_iters"][k] == r["alp_iters"], ctx
-                assert st["alp_switch"][k] == r["alp_switch"], ctx
-                assert st["lp_rows_final"][k] == r["lp_rows_final"], ctx
+                ctx = (eb, r["frame"])
+                bad = []
+                if st["status"][k] != r["status"]:
+                    bad.append(f"status {st['status'][k]} vs {r['status']}")
+                if not np.array_equal(h[k], r["hard_v"]):
+                    bad.append("hard")
+                if c[k] != r["cert"]:
+                    bad.append("cert")
                 du = float(np.max(np.abs(u[k] - r["u_v"])))
                 worst_u = max(worst_u, du)
-                assert du <= 1e-6, (ctx, du)
-                assert abs(st["objective"][k] - r["objective"]) <= \
-                    1e-6 * (1 + abs(r["objective"])), ctx
+                if du > 1e-6:
+                    bad.append(f"u {du:.1e}")
+                if abs(st["objective"][k] - r["objective"]) > 1e-6 * (1 + abs(r["objective"])):
+                    bad.append("objective")
+                if not np.array_equal(mk[k], r["masks_v"]):
+                    bad.append(f"cut set ({int((mk[k] != r['masks_v']).sum())} checks)")
+                for fld in ("alp_iters", "alp_switch", "lp_rows_final"):
+                    if st[fld][k] != r[fld]:
+                        bad.append(f"{fld} {st[fld][k]} vs {r[fld]}")
+                if bad:
+                    failures.append((ctx, bad))
     print(f"precision {precision}: max |u - u_oracle| = {worst_u:.3e}")
+    assert not failures, failures

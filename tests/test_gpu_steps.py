@@ -70,30 +70,82 @@ def test_cut_search_bit_exact(dec120):
         assert g_flag[f] == e_add
 
 
-def test_mts_selection_bit_exact(dec120):
+@pytest.mark.parametrize("kind", [L.LPDEC_MTS_COLUMN, L.LPDEC_MTS_INCREMENTAL,
+                                  L.LPDEC_MTS_ROWWISE])
+def test_mts_selection_bit_exact(kind):
+    """Algorithms 7 (column-wise), 6 with 5 (incremental) and 8 (row-wise
+    with diagonal expansion): the selected (column, row) pairs in selection
+    order equal the oracle's, on LPs of oracle decodes with random weights,
+    quantised weights (ties) and weights that differ below single
+    precision."""
     torch = torch_cuda()
     code, recs = oracle_history("gallager_120", 2.0, 0, 12)
     g, in_lp, mask, lps = lp_state_arrays(code, recs)
     nf = len(lps)
     qm = code.n + code.m
-    rng = np.random.default_rng(9)
+    rng = np.random.default_rng(7)
     W = np.zeros((nf, qm))
     for f, lp in enumerate(lps):
         w = np.exp(rng.normal(size=lp.q) * 5)
         if f % 3 == 0:                       # ties: quantised weights
             w = np.round(rng.random(lp.q) * 4) + 1
+        elif f % 3 == 1:                     # differences below single precision
+            w = 1.0 + rng.integers(0, 4, size=lp.q) * 1e-12
         W[f, :lp.q] = w
-    d_col = torch.empty((nf, code.m), dtype=torch.int32, device="cuda")
-    d_row = torch.empty((nf, code.m), dtype=torch.int32, device="cuda")
-    rc = L.lpdec_mts_select_device(dec120.ctx, dec120.code, nf, dev(g), dev(in_lp), dev(mask),
-                                   dev(W), d_col, d_row)
-    assert rc == 0
-    col, row = host(d_col), host(d_row)
+    prm = L.lpdec_default_params()
+    prm.precond = kind
+    with L.Decoder(code, params=prm) as d:
+        d_col = torch.empty((nf, code.m), dtype=torch.int32, device="cuda")
+        d_row = torch.empty((nf, code.m), dtype=torch.int32, device="cuda")
+        rc = L.lpdec_mts_select_device(d.ctx, d.code, nf, dev(g), dev(in_lp), dev(mask),
+                                       dev(W), d_col, d_row)
+        assert rc == 0
+        col, row = host(d_col), host(d_row)
     for f, lp in enumerate(lps):
-        ec, er = omts.colwise(lp.A, W[f, :lp.q], f32=True)
-        assert np.array_equal(col[f, :lp.p], ec), f
-        assert np.array_equal(row[f, :lp.p], er), f
+        w = W[f, :lp.q]
+        if kind == L.LPDEC_MTS_COLUMN:
+            ec, er = omts.colwise(lp.A, w)
+        elif kind == L.LPDEC_MTS_INCREMENTAL:
+            ec, er = omts.incremental(lp.A, w)
+        else:
+            ec, er = omts.rowwise(lp.A, w, code.n)
+        assert np.array_equal(col[f, :lp.p], ec), (kind, f)
+        assert np.array_equal(row[f, :lp.p], er), (kind, f)
         assert np.all(col[f, lp.p:] == -1)
+
+
+@pytest.mark.parametrize("kind", [L.LPDEC_MTS_INCREMENTAL, L.LPDEC_MTS_ROWWISE])
+def test_pcg_with_each_preconditioner_matches_dense_solve(kind):
+    """PCG (Algorithm 4) preconditioned by the incremental and row-wise
+    triangular sets (lower triangular: the level schedules run in the other
+    directions) solves the Newton system as a dense solve does."""
+    torch = torch_cuda()
+    code, recs = oracle_history("gallager_120", 2.0, 0, 12)
+    g, in_lp, mask, lps = lp_state_arrays(code, recs)
+    nf = len(lps)
+    qm = code.n + code.m
+    rng = np.random.default_rng(13)
+    D2 = np.zeros((nf, qm))
+    Wv = np.zeros((nf, code.m))
+    for f, lp in enumerate(lps):
+        D2[f, :lp.q] = np.exp(rng.normal(size=lp.q) * 2)
+        Wv[f, :lp.p] = rng.normal(size=lp.p)
+    prm = L.lpdec_default_params()
+    prm.precond = kind
+    with L.Decoder(code, params=prm) as d:
+        d_dy = torch.zeros((nf, code.m), dtype=torch.float64, device="cuda")
+        d_it = torch.zeros(nf, dtype=torch.int32, device="cuda")
+        rc = L.lpdec_pcg_device(d.ctx, d.code, nf, dev(g), dev(in_lp), dev(mask), dev(D2),
+                                dev(Wv), d_dy, d_it)
+        assert rc == 0
+        dy, its = host(d_dy), host(d_it)
+    for f, lp in enumerate(lps):
+        Q = (lp.A * D2[f, :lp.q]) @ lp.A.T
+        ref = np.linalg.solve(Q, Wv[f, :lp.p])
+        rel = np.linalg.norm(dy[f, :lp.p] - ref) / np.linalg.norm(ref)
+        kappa = np.linalg.cond(Q)
+        assert rel <= max(1e-8, 1e-10 * kappa * 10), (kind, f, rel, kappa, its[f])
+        assert its[f] <= lp.p + 5
 
 
 def test_pcg_matches_dense_solve(dec120):

@@ -65,6 +65,11 @@ def test_hamming74_pseudocodeword():
     assert np.max(np.abs(res.u - np.array(g["u_expected"]))) < 1e-9
     assert res.cert == g["cert_expected"]
     assert int(np.sum(np.abs(res.u - np.round(res.u)) > 1e-6)) == code.m
+    # hard decision of a fractional output (the paper only declares failure):
+    # [u_i > 1/2], and the channel's decision [gamma_i < 0] on the three
+    # entries at exactly 1/2 (gamma = 1, -1, -2 there). Plain rounding would
+    # give [1, 0, 0, 0, 0, 0, 0].
+    assert res.hard.tolist() == [1, 0, 0, 1, 0, 0, 1]
 
 
 def _peel(H, E):
@@ -235,3 +240,29 @@ def test_theorem_2d_each_lp_solves_lp_decoding_of_its_active_checks():
             assert np.max(np.abs(h.u - u_ref)) < 1e-7
             checked += 1
     assert checked >= 20
+
+
+def _decode_pair(code, G, prm):
+    return [oracle.decode(code, g, prm) for g in G]
+
+
+@pytest.mark.parametrize("name,nframes", [("gallager_120", 60), ("gallager_480", 12)])
+def test_open_readings_do_not_change_results(name, nframes):
+    """Two readings of the points the paper leaves open change no decoded
+    result on the workloads: the looser feasibility test once the gap is
+    small (tol_feas_loose) and the interior-point cap of 60. Whole decodes
+    with tol_feas_loose = tol_feas (the loose test off) and max_ipm = 200 give
+    the same decisions, and u within 1e-9."""
+    code = named_code(name)
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(nframes))
+    base = _decode_pair(code, G, OracleParams())
+    strict = _decode_pair(code, G, OracleParams(tol_feas_loose=OracleParams().tol_feas,
+                                                max_ipm=200))
+    n_lp = 0
+    for a, b in zip(base, strict):
+        assert a.status == b.status == 0
+        assert np.array_equal(a.hard, b.hard) and a.cert == b.cert
+        assert np.array_equal(a.masks, b.masks) and a.alp_iters == b.alp_iters
+        assert np.max(np.abs(a.u - b.u)) < 1e-9
+        n_lp += a.alp_iters
+    assert n_lp > nframes
