@@ -886,7 +886,9 @@ __device__ inline Levels mts_rowwise(Blk& B, const CodeView& C, WS<T>& W, const 
                     int c = (t < d) ? (W.rowent[e0 + t] & kIdx) : n + (int)j;
                     if (W.deg[c]) cand = min(cand, (unsigned)c);
                 }
-                victim = (int)__reduce_min_sync(kFull, cand);
+                const unsigned vu = __reduce_min_sync(kFull, cand);
+                if (vu == 0xffffffffu) break;   // cannot happen (see above)
+                victim = (int)vu;
                 if (lane == 0) {
                     W.pivcol[j] = (uint16_t)victim;
                     W.pivrow[victim] = (uint16_t)j;
@@ -897,6 +899,7 @@ __device__ inline Levels mts_rowwise(Blk& B, const CodeView& C, WS<T>& W, const 
                 // least weight, then lowest index: the first live entry of
                 // the run of equal weights that ends at the last live entry
                 while (lo >= 0 && !W.deg[W.sorted[lo]]) --lo;
+                if (lo < 0) break;              // cannot happen: a live column is left
                 int t = lo;
                 const double wl = wt[W.sorted[lo]];
                 while (t > 0 && wt[W.sorted[t - 1]] == wl) --t;
@@ -1001,7 +1004,9 @@ __device__ inline int peel_set(Blk& B, WS<T>& W, int n, int p, int s, uint16_t s
             int c = (t < d) ? (W.rowent[e0 + t] & kIdx) : n + j;
             if (W.rank[c] == stamp) cand = min(cand, (unsigned)c);
         }
-        const int x = (int)__reduce_min_sync(kFull, cand);
+        const unsigned xu = __reduce_min_sync(kFull, cand);
+        if (xu == 0xffffffffu) break;   // cannot happen: a degree-1 row holds one live column
+        const int x = (int)xu;
         __syncwarp();
         if (lane == 0) {
             W.rank[x] = 0;
