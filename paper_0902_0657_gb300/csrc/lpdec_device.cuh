@@ -1125,6 +1125,22 @@ __device__ inline Levels mts_incremental(Blk& B, const CodeView& C, WS<T>& W, co
             W.pivrow[x] = (uint16_t)j;
             W.selrow[t] = (uint16_t)j;
         }
+        __syncwarp();
+        // (defensive: Algorithm 6 always keeps p columns; a row left without
+        // a pivot would take its own slack column, which keeps the set
+        // triangular)
+        int k = peeled;
+        for (int base = 0; base < p; base += 32) {
+            const int j = base + lane;
+            const bool need = j < p && W.pivcol[j] == kNone;
+            const unsigned bal = __ballot_sync(kFull, need);
+            if (need) {
+                W.pivcol[j] = (uint16_t)(n + j);
+                W.pivrow[n + j] = (uint16_t)j;
+                W.selrow[k + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)j;
+            }
+            k += __popc(bal);
+        }
     }
     __syncthreads();
     return finish_levels<T>(B, C, W, F, true);
