@@ -69,6 +69,8 @@ def parse_args():
                     help="fp64: FP64 PCG; mixed: FP32 PCG refined in FP64; "
                          "m32: FP64 PCG with an FP32 preconditioner solve")
     ap.add_argument("--threads", type=int, default=128)
+    ap.add_argument("--precond", choices=["column", "incremental", "rowwise", "adaptive"],
+                    default="column", help="triangular-set preconditioner (Section V)")
     ap.add_argument("--smem-budget", type=int, default=0,
                     help="shared-memory bytes per CTA (0 = library choice)")
     ap.add_argument("--ebn0", type=float, default=EBN0_DB,
@@ -91,7 +93,7 @@ def workload_config(args, n, m):
         "code": CODE_NAME, "n": n, "m": m, "ebn0_db": args.ebn0, "pool_frames": POOL,
         "frames_per_step": args.frames, "warmup_frames_per_step": args.warmup_frames,
         "precision": args.precision, "smem_budget": args.smem_budget or "library (1/3 of SM)",
-        "threads_per_block": args.threads, "variant": "MALP-A",
+        "threads_per_block": args.threads, "variant": "MALP-A", "precond": args.precond,
         "l2": "flushed by a 256 MB write between timed steps",
     }
 
@@ -228,6 +230,8 @@ def run_ours(args):
     prm.precision = {"fp64": L.LPDEC_FP64, "mixed": L.LPDEC_MIXED, "m32": L.LPDEC_M32}[args.precision]
     prm.threads_per_block = args.threads
     prm.smem_budget = args.smem_budget
+    prm.precond = {"column": L.LPDEC_MTS_COLUMN, "incremental": L.LPDEC_MTS_INCREMENTAL,
+                   "rowwise": L.LPDEC_MTS_ROWWISE, "adaptive": L.LPDEC_MTS_ADAPTIVE}[args.precond]
     dec = L.Decoder(code, device=local, params=prm)
 
     nsteps = args.warmup + args.steps
