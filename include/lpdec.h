@@ -131,7 +131,11 @@ extern "C" {
  * The decisions are taken on the LP's optimal vertex, recovered from the
  * final interior-point iterate through its strictly complementary
  * partition (basic iff x_i > z_i, Section VI-A) and certified optimal by a
- * primal-dual feasible, complementary pair.
+ * primal-dual feasible, complementary pair. An iterate whose partition does
+ * not certify (it has not separated yet) is refined by solving the LP again
+ * at a 100x, then 1000x tighter gap with twice max_ipm; an LP that still
+ * cannot be certified keeps the partition's vertex and counts in
+ * stats.vertex_failures.
  */
 typedef struct lpdec_params {
     double sigma, eta, tol_gap, tol_feas, tol_pcg, tau_act, tau_cut, tau_int;
@@ -157,7 +161,7 @@ typedef struct lpdec_stats {
     int32_t ipm_iters_total;  /* interior-point iterations over all LPs */
     int32_t pcg_iters_total;  /* PCG iterations over all Newton steps */
     int32_t lp_rows_final;    /* p of the last LP (parity inequalities) */
-    int32_t vertex_failures;  /* LPs whose optimal-vertex recovery was rejected */
+    int32_t vertex_failures;  /* LPs whose vertex could not be certified optimal */
     int32_t max_levels;       /* deepest triangular-solve level schedule seen */
     int32_t pcg_iters_fp64;   /* PCG iterations run in FP64 (all of them in LPDEC_FP64) */
     int32_t dense_solves;     /* Newton systems solved by the dense Cholesky fallback */
@@ -369,44 +373,68 @@ int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
                                           void* stream);
 
 /* ---------------------------------------------------------------------------
- * Serving: frames submitted one at a time as they arrive, decoded in batches
- * that overlap on the GPU. The paper has no counterpart (it decodes one frame
- * at a time); each frame is still decoded by Algorithm 3 exactly as by
- * lpdec_decode, and its result does not depend on the frames it is batched
- * with.
+ * Serving: continuous batching. The paper decodes one frame at a time and
+ * has no counterpart; each frame is still decoded by Algorithm 3 exactly as
+ * by lpdec_decode, and its result does not depend on the frames it shares
+ * the GPU with.
  *
- * A server owns `lanes` decoder contexts on `device` (each with its own
- * stream, scratch and copy of the code H given in CSR as for
- * lpdec_code_create), each with buffers for `batch` frames. A worker thread
- * starts a batch of queued frames on every idle lane; while one lane's batch
- * finishes its slowest frames, the next lane's batch takes the SMs it frees.
- * `params` as for lpdec_ctx_create (NULL = defaults). At most `max_pending`
- * submitted frames may be outstanding (queued, running, or finished and not
- * yet polled). Device memory: about lanes x (scratch of a full grid + 2 x
- * batch x (9n + 64) bytes). Returns LPDEC_ERR_NO_DEVICE without a usable
- * GPU, LPDEC_ERR_INVALID_ARG for bad arguments (lanes 1..16, batch >= 1,
- * max_pending >= 1, a CSR as for lpdec_code_create). */
+ * A server decodes frames of the codes it is created with (any lengths) as
+ * they are submitted. One persistent kernel runs while frames are queued;
+ * its CTAs take the next queued frame as soon as they finish one, so a frame
+ * submitted while others run starts as soon as a CTA frees up, and the
+ * kernel ends by itself once no frame has arrived for a short idle time
+ * (the server starts it again on the next submission). Frames are admitted
+ * by device-memory bytes: each frame holds a region of the server's arena
+ * (its LLRs in, its results out: about 17 n + 4 m bytes) from submission
+ * until its results are copied back, and a submission that does not fit is
+ * refused. All waits inside the kernel are bounded.
+ *
+ * lpdec_server_create: codes[ncodes] (from lpdec_code_create, on `device`;
+ * they must outlive the server); params as for lpdec_ctx_create (NULL =
+ * defaults); hbm_budget_bytes bounds the device memory of the server, its
+ * per-CTA scratch included (0: an arena for max_pending frames of the
+ * largest code); max_pending (1 .. 2^20) bounds the frames queued or running.
+ * Returns LPDEC_ERR_OUT_OF_BUDGET when the budget does not cover the
+ * scratch plus one frame, LPDEC_ERR_NO_DEVICE without a usable GPU,
+ * LPDEC_ERR_INVALID_ARG for bad arguments. */
 typedef struct lpdec_server lpdec_server;
-int32_t lpdec_server_create(int32_t device, const lpdec_params* params, int32_t m, int32_t n,
-                            const int32_t* row_ptr, const int32_t* col_idx, int32_t lanes,
-                            int32_t batch, int32_t max_pending, lpdec_server** out);
+int32_t lpdec_server_create(int32_t device, const lpdec_params* params, int32_t ncodes,
+                            const lpdec_code* const* codes, size_t hbm_budget_bytes,
+                            int32_t max_pending, lpdec_server** out);
 
-/* Queues one frame: gamma = n host FP64 LLRs (copied before return). Writes
- * the frame's ticket (0, 1, 2, ... in submission order). Returns
- * LPDEC_ERR_OUT_OF_BUDGET when max_pending frames are outstanding,
- * LPDEC_ERR_INVALID_ARG for a non-finite LLR, or the server's sticky error
- * after a failed CUDA call. */
-int32_t lpdec_submit(lpdec_server* server, const double* gamma, uint64_t* ticket);
+/* Queues one frame of `code` (one of the server's codes): gamma = n host
+ * FP64 LLRs, copied to the device before return. Writes the frame's ticket
+ * (0, 1, 2, ... in submission order). Returns LPDEC_ERR_OUT_OF_BUDGET when
+ * the frame's region does not fit the arena or max_pending frames are
+ * queued or running, LPDEC_ERR_INVALID_ARG for a non-finite LLR or a code
+ * the server was not created with, or the server's sticky error after a
+ * failed CUDA call. */
+int32_t lpdec_submit(lpdec_server* server, const lpdec_code* code, const double* gamma,
+                     uint64_t* ticket);
 
-/* Result of one ticket, once: u (n FP64), hard (n bytes), cert and stats
- * (any output may be NULL), then the ticket is released. Returns
- * LPDEC_ERR_PENDING while the frame is queued or running,
- * LPDEC_ERR_INVALID_ARG for a ticket never issued or already polled, or the
- * server's sticky error. Never blocks on the GPU. */
+/* Result of one ticket, once: u (n FP64), hard (n bytes), cert, cut mask
+ * (m words) and stats (any output may be NULL); then the ticket is
+ * released. Returns LPDEC_ERR_PENDING while the frame is queued or running,
+ * LPDEC_ERR_INVALID_ARG for a ticket never issued, already polled or
+ * cancelled, or the server's sticky error. Never blocks on the GPU. */
 int32_t lpdec_poll(lpdec_server* server, uint64_t ticket, double* u_out, uint8_t* hard_out,
-                   int32_t* cert_out, lpdec_stats* stats);
+                   int32_t* cert_out, uint32_t* cut_mask_out, lpdec_stats* stats);
 
-/* Drops the queued frames, waits for the running batches, frees everything. */
+/* Cancels a ticket: a frame no CTA has taken yet is skipped, a running one
+ * runs to its end; either way its result is dropped and its region and
+ * ticket are released (no poll needed). LPDEC_ERR_INVALID_ARG for a ticket
+ * never issued, polled or cancelled. */
+int32_t lpdec_cancel(lpdec_server* server, uint64_t ticket);
+
+/* Device bytes the server holds (scratch + arena), the arena's size, the
+ * arena bytes held by frames, and the tickets not yet polled or released
+ * (any output may be NULL). A frame of a code with n bits and m checks
+ * holds 8n (LLRs) + 8n (u) + n (hard) + 4m (cut mask) + 4 (cert) bytes and
+ * one lpdec_stats, each part 16-byte aligned, rounded up to 256 bytes. */
+int32_t lpdec_server_stats(lpdec_server* server, size_t* hbm_bytes, size_t* arena_bytes,
+                           size_t* arena_used, int32_t* outstanding);
+
+/* Stops the kernel, drops queued frames and frees everything. */
 int32_t lpdec_server_destroy(lpdec_server* server);
 
 #ifdef __cplusplus

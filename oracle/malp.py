@@ -154,7 +154,17 @@ def decode(code, gamma, params: OracleParams | None = None,
         res = _ipm.solve(lp.A, lp.b, lp.c, prm, solve_normal=solver)
         lps += 1
         ipm_total += res.iters
-        xv, vok = _vertex.recover(lp.A, lp.b, lp.c, res.x, res.z)
+        xv, vok = _vertex.recover(lp.A, lp.b, lp.c, res.x, res.z, res.y)
+        # an iterate that has not separated the optimal partition yet: resume
+        # the method with a tighter gap until the vertex is certified optimal
+        for scale in (1e-2, 1e-3):
+            if vok or res.status != OK:
+                break
+            tight = dataclasses.replace(prm, tol_gap=prm.tol_gap * scale,
+                                        max_ipm=2 * prm.max_ipm)
+            res = _ipm.solve(lp.A, lp.b, lp.c, tight, solve_normal=solver)
+            ipm_total += res.iters
+            xv, vok = _vertex.recover(lp.A, lp.b, lp.c, res.x, res.z, res.y)
         vfail += int(not vok)
         u = lp.u_from_x(xv)
         s_rows = xv[n:]

@@ -40,7 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + ".tmp"
-    units = [os.path.join(SRC, f) for f in ("lpdec.cu", "serve.cu")]
+    units = [os.path.join(SRC, "lpdec.cu")]
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
            "-Xcompiler", "-fPIC", "-o", tmp, *units]
     if verbose:

@@ -4,12 +4,17 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lpdec_device.cuh"
@@ -26,6 +31,8 @@ struct KernelShared {
     int shscan[40];
     int next;
     int sw;
+    long long qoff;   // serving: the claimed queue entry, read once by thread 0
+    int qcode, qcancel;
 };
 
 // The warp of this CTA that runs its single-warp phases. A CTA's warps take
@@ -221,17 +228,23 @@ k_lp_solve(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_
         lp_build<T>(B, C, W, F, ks.shscan, false, C.pmax, C.eamax);
         lpdec_stats st{};
         if (F.p > 0) {
-            IpmOut io = ipm_solve<T>(B, C, W, F, P, g, 0,
-                                     trace ? trace + (size_t)f * 8 * max_trace : nullptr,
-                                     max_trace);
-            int ok = io.certified || certify<T>(B, C, W, F, g);
-            if (!ok) st.vertex_failures = vertex_recover<T>(B, C, W, F, g);
+            IpmOut io;
+            bool solved;
+            if (trace) {   // one run, traced (no refinement)
+                io = ipm_solve<T>(B, C, W, F, P, g, 0, trace + (size_t)f * 8 * max_trace,
+                                  max_trace);
+                int ok = io.certified || certify<T>(B, C, W, F, g);
+                if (!ok) st.vertex_failures = vertex_recover<T>(B, C, W, F, g);
+                solved = io.converged || ok;
+            } else {
+                solved = solve_lp<T>(B, C, W, F, P, g, st, io);
+            }
             st.ipm_iters_total = io.iters;
             st.pcg_iters_total = io.pcg_iters;
             st.pcg_iters_fp64 = io.pcg_iters64;
             st.pcg_flops = io.flops;
             st.max_levels = io.max_levels;
-            st.status = (io.converged || ok) ? LPDEC_OK : LPDEC_ERR_NOT_CONVERGED;
+            st.status = solved ? LPDEC_OK : LPDEC_ERR_NOT_CONVERGED;
         } else {
             for (int i = B.tid; i < C.n; i += B.nt) W.x[i] = 0.0;
             __syncthreads();
@@ -414,6 +427,7 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
         {G_P64, real_bytes < 8 ? D * vec_elems(n, pm) : 16, 2},
         {G_QD, dense_rows > 0 ? D * (size_t)dense_rows * dense_rows : 16, 2},
         {G_CCHK2, H * P, 2}, {G_CMASK2, I * P, 2}, {G_CRPTR2, I * ((size_t)m + 1), 2},
+        {G_GAM, D * (size_t)n, 2},
     };
     Layout L{};
     size_t s = 0, g = 0;
@@ -1259,3 +1273,5 @@ extern "C" int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
     CK(cudaGetLastError());
     return LPDEC_OK;
 }
+
+#include "serve.cuh"

@@ -78,6 +78,9 @@ enum Arr {
     G_QD,
     // cut list being rebuilt (rows, masks, per-check row pointers) after a cut search
     G_CCHK2, G_CMASK2, G_CRPTR2,
+    // the CTA's copy of the frame's LLRs (serving: read from the shared arena
+    // once, past the SM's L1)
+    G_GAM,
     A_COUNT
 };
 
@@ -111,7 +114,7 @@ struct Layout {
 __host__ __device__ constexpr bool row_sized(int a) {
     return !(a == S_FLAGS || a == S_MASK || a == S_FLIP || a == S_HPTR || a == S_VPTR ||
              a == S_CPTR || a == S_CRPTR || a == G_U || a == G_T64 || a == G_QD ||
-             a == G_CRPTR2);
+             a == G_CRPTR2 || a == G_GAM);
 }
 
 template <typename T>
@@ -131,6 +134,7 @@ struct WS {
     double *x, *zz, *rc, *d2, *y, *b, *w, *dy, *r64, *u, *t64;
     double *vx, *v1, *v2, *v3, *v4, *vr1, *vr2, *p64;
     double* qd;   // dense Cholesky factor (column-major p x p), null when off
+    double* gam;  // private copy of the frame's LLRs (serving)
     uint16_t* cchk2;
     uint32_t *cmask2, *crptr2;
     int cap_n, cap_p;   // capacities the sub-arrays were sliced with
@@ -183,6 +187,7 @@ __device__ inline void point_ws(WS<T>& w, const Layout& L, char* smem, char* gws
     P_(double, qd, G_QD);
     P_(uint16_t, cchk2, G_CCHK2); P_(uint32_t, cmask2, G_CMASK2);
     P_(uint32_t, crptr2, G_CRPTR2);
+    P_(double, gam, G_GAM);
 #undef P_
     if (!only_rows) {
         if (!L.dense) w.qd = nullptr;
@@ -227,7 +232,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W) {
     v.x = W.x; v.zz = W.zz; v.rc = W.rc; v.d2 = W.d2; v.y = W.y; v.b = W.b; v.w = W.w;
     v.dy = W.dy; v.r64 = W.r64; v.u = W.u; v.t64 = W.t64;
     v.vx = W.vx; v.v1 = W.v1; v.v2 = W.v2; v.v3 = W.v3; v.v4 = W.v4; v.vr1 = W.vr1;
-    v.vr2 = W.vr2; v.p64 = W.p64; v.qd = W.qd;
+    v.vr2 = W.vr2; v.p64 = W.p64; v.qd = W.qd; v.gam = W.gam;
     v.cchk2 = W.cchk2; v.cmask2 = W.cmask2; v.crptr2 = W.crptr2;
     return v;
 }
@@ -747,7 +752,7 @@ __device__ inline void back_levels(Blk& B, WS<T>& W, int p) {
 }
 
 template <typename T>
-__device__ inline Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                     const double* wt, int /*q2*/) {
     const int n = C.n, p = F.p, q = F.q;
     for (int i = B.tid; i < q; i += B.nt) {
@@ -854,7 +859,7 @@ __device__ __forceinline__ void bit_clear(uint32_t* bm, int i) { atomicAnd(&bm[i
 // computed.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ inline Levels mts_rowwise(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ Levels mts_rowwise(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                      const double* wt) {
     const int n = C.n, p = F.p, q = F.q;
     uint16_t* rowdeg = W.lb;
@@ -1042,7 +1047,7 @@ __device__ inline int peel_set(Blk& B, WS<T>& W, int n, int p, int s, uint16_t s
 }
 
 template <typename T>
-__device__ inline Levels mts_incremental(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ Levels mts_incremental(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                          const double* wt) {
     const int n = C.n, p = F.p, q = F.q;
     uint16_t* rowcnt = W.lb;
@@ -1530,7 +1535,7 @@ constexpr double kPivotTiny = 1e-13;
 constexpr double kPivotHuge = 1e64;
 
 template <typename T>
-__device__ inline bool dense_newton(Blk& B, const CodeView& C, WS<T>& W, const Frame& F) {
+__device__ __noinline__ bool dense_newton(Blk& B, const CodeView& C, WS<T>& W, const Frame& F) {
     const int n = C.n, p = F.p;
     double* Lm = W.qd;
     const size_t pp = (size_t)p * p;
@@ -1599,7 +1604,7 @@ __device__ inline bool dense_newton(Blk& B, const CodeView& C, WS<T>& W, const F
 }
 
 template <typename T>
-__device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                          const Levels& L, const DevParams& P, double tol,
                                          int max_it, bool& force64, bool& force_dense) {
     const int p = F.p;
@@ -1720,7 +1725,7 @@ __device__ __forceinline__ double cost_of(const double* gamma, int n, int i) {
 }
 
 template <typename T>
-__device__ inline int certify(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ int certify(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                               const double* gamma) {
     const int n = C.n, p = F.p, q = F.q;
     double nbasic = 0.0, cmax = 0.0;
@@ -1850,7 +1855,7 @@ __device__ inline int certify(Blk& B, const CodeView& C, WS<T>& W, const Frame& 
 // and dual feasible and complementary, so x^ is optimal (and, the optimum
 // being unique, the vertex the oracle reaches). On success x := x^.
 template <typename T>
-__device__ inline int certify_basis(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ int certify_basis(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                     const Levels& L, const double* gamma) {
     const int n = C.n, p = F.p, q = F.q;
     WS<double> D = fp64_view<T>(W);
@@ -1908,7 +1913,7 @@ struct IpmOut {
 // trace (optional): per iteration 8 doubles {gap, feas_p, feas_d, PCG
 // iterations, Newton relative residual, beta_P, beta_D, levels}
 template <typename T>
-__device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F,
+__device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F,
                                    const DevParams& P, const double* gamma, int q2,
                                    double* trace = nullptr, int max_trace = 0) {
     const int n = C.n, p = F.p, q = F.q;
@@ -2069,7 +2074,7 @@ __device__ inline IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F
 // over rows (W.w, W.r64).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ inline int vertex_recover(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ int vertex_recover(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                      const double* gamma) {
     const int n = C.n, p = F.p, q = F.q;
     double* d = W.rc;
@@ -2163,6 +2168,38 @@ __device__ inline int vertex_recover(Blk& B, const CodeView& C, WS<T>& W, const 
     }
     __syncthreads();
     return ok ? 0 : 1;
+}
+
+// One LP of the adaptive loop: the interior-point method, then its vertex
+// with an optimality certificate. An iterate that has not separated the
+// optimal partition yet (the certificate fails although the method
+// converged) is refined by solving again at a 100x, then 1000x tighter gap
+// (twice the iteration cap); only if that fails too is the partition's
+// vertex taken without a certificate (counted in vertex_failures). Returns
+// whether the LP ended converged or certified; io accumulates the counts.
+template <typename T>
+__device__ inline bool solve_lp(Blk& B, const CodeView& C, WS<T>& W, Frame& F,
+                                const DevParams& P, const double* gamma, lpdec_stats& st,
+                                IpmOut& io) {
+    io = ipm_solve<T>(B, C, W, F, P, gamma, 0);
+    int ok = io.certified || certify<T>(B, C, W, F, gamma);
+    DevParams Q = P;
+    Q.max_ipm = 2 * P.max_ipm;
+    for (int k = 0; k < 2 && !ok && io.converged; ++k) {
+        Q.tol_gap = P.tol_gap * (k == 0 ? 1e-2 : 1e-3);
+        IpmOut o2 = ipm_solve<T>(B, C, W, F, Q, gamma, 0);
+        o2.iters += io.iters;
+        o2.pcg_iters += io.pcg_iters;
+        o2.pcg_iters64 += io.pcg_iters64;
+        o2.dense += io.dense;
+        o2.flops += io.flops;
+        o2.bytes += io.bytes;
+        o2.max_levels = max(o2.max_levels, io.max_levels);
+        io = o2;
+        ok = io.certified || certify<T>(B, C, W, F, gamma);
+    }
+    if (!ok) st.vertex_failures += vertex_recover<T>(B, C, W, F, gamma);
+    return io.converged || ok;
 }
 
 // u from x (undo the flip of Eq. 16) and the active flags of the LP rows.
@@ -2259,7 +2296,8 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, const WS<T>& W0,
             built = lp_build<T>(B, C, W, F, shscan, alp, C.pwide, C.eawide);
         }
         if (!built) { status = LPDEC_ERR_OUT_OF_BUDGET; break; }
-        IpmOut io = ipm_solve<T>(B, C, W, F, P, gamma, q2);
+        IpmOut io;
+        const bool solved = solve_lp<T>(B, C, W, F, P, gamma, st, io);
         st.alp_iters++;
         st.ipm_iters_total += io.iters;
         st.pcg_iters_total += io.pcg_iters;
@@ -2268,11 +2306,9 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, const WS<T>& W0,
         st.pcg_flops += io.flops;
         st.pcg_bytes += io.bytes;
         st.max_levels = max(st.max_levels, io.max_levels);
-        int ok = io.certified || certify<T>(B, C, W, F, gamma);
-        if (!ok) st.vertex_failures += vertex_recover<T>(B, C, W, F, gamma);
         lp_finish<T>(B, C, W, F, P);
         st.lp_rows_final = F.p;
-        if (!io.converged && !ok) { status = LPDEC_ERR_NOT_CONVERGED; break; }
+        if (!solved) { status = LPDEC_ERR_NOT_CONVERGED; break; }
         // Theorem 2(b): with unique LP optima the MALP cost rises strictly. A
         // cost that does not rise means that hypothesis failed and MALP may
         // cycle between cut sets short of the optimum; the frame continues as

@@ -110,12 +110,17 @@ def _load():
     lib.lpdec_lp_solve_trace_device.argtypes = [P, P, i32, P, P, P, P, P, P, i32, P]
     lib.lpdec_decode_batch_device_noalloc.argtypes = [P, ctypes.POINTER(lpdec_params), i32, P, P,
                                                       P, P, P, P, P]
-    lib.lpdec_server_create.argtypes = [i32, ctypes.POINTER(lpdec_params), i32, i32, P, P, i32,
-                                        i32, i32, ctypes.POINTER(P)]
-    lib.lpdec_submit.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
-    lib.lpdec_poll.argtypes = [P, ctypes.c_uint64, P, P, P, P]
+    lib.lpdec_server_create.argtypes = [i32, ctypes.POINTER(lpdec_params), i32, P,
+                                        ctypes.c_size_t, i32, ctypes.POINTER(P)]
+    lib.lpdec_submit.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.lpdec_poll.argtypes = [P, ctypes.c_uint64, P, P, P, P, P]
+    lib.lpdec_cancel.argtypes = [P, ctypes.c_uint64]
+    lib.lpdec_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i32)]
     lib.lpdec_server_destroy.argtypes = [P]
-    for name in ("lpdec_server_create", "lpdec_submit", "lpdec_poll", "lpdec_server_destroy"):
+    for name in ("lpdec_server_create", "lpdec_submit", "lpdec_poll", "lpdec_cancel",
+                 "lpdec_server_stats", "lpdec_server_destroy"):
         getattr(lib, name).restype = i32
     for name in ("lpdec_ctx_create", "lpdec_ctx_set_params", "lpdec_code_create",
                  "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_frames",
@@ -404,33 +409,60 @@ class Decoder:
 
 
 # ---------------------------------------------------------------------------
-# Serving (lpdec_server_create / lpdec_submit / lpdec_poll)
+# Serving (lpdec_server_create / lpdec_submit / lpdec_poll / lpdec_cancel)
 # ---------------------------------------------------------------------------
 
-def lpdec_server_create(device: int, params: lpdec_params | None, code, lanes: int = 2,
-                        batch: int = 512, max_pending: int = 1 << 16):
-    rp = np.ascontiguousarray(code.row_ptr, dtype=np.int32)
-    ci = np.ascontiguousarray(code.col_idx, dtype=np.int32)
+def lpdec_server_create(device: int, params: lpdec_params | None, code_handles,
+                        hbm_budget_bytes: int = 0, max_pending: int = 1 << 16):
+    nc = len(code_handles)
+    arr = (ctypes.c_void_p * nc)(*code_handles)
     out = ctypes.c_void_p()
     rc = _load().lpdec_server_create(device, ctypes.byref(params) if params is not None else None,
-                                     code.m, code.n, rp.ctypes.data, ci.ctypes.data, lanes,
-                                     batch, max_pending, ctypes.byref(out))
+                                     nc, arr, hbm_budget_bytes, max_pending, ctypes.byref(out))
     _check(rc, "lpdec_server_create")
     return out.value
 
 
-def lpdec_submit(server, gamma) -> tuple[int, int]:
+def lpdec_submit(server, code_handle, gamma) -> tuple[int, int]:
     """Returns (status, ticket)."""
     g = np.ascontiguousarray(gamma, dtype=np.float64)
     t = ctypes.c_uint64()
-    rc = _load().lpdec_submit(server, g.ctypes.data, ctypes.byref(t))
+    rc = _load().lpdec_submit(server, code_handle, g.ctypes.data, ctypes.byref(t))
     return rc, t.value
 
 
-def lpdec_poll(server, ticket: int, u_out=None, hard_out=None, cert_out=None, stats_out=None):
+def lpdec_poll(server, ticket: int, u_out=None, hard_out=None, cert_out=None, cut_mask_out=None,
+               stats_out=None):
     return _load().lpdec_poll(server, ticket, _hptr(u_out, np.float64),
                               _hptr(hard_out, np.uint8), _hptr(cert_out, np.int32),
+                              _hptr(cut_mask_out, np.uint32),
                               None if stats_out is None else stats_out.ctypes.data)
+
+
+def lpdec_cancel(server, ticket: int) -> int:
+    return _load().lpdec_cancel(server, ticket)
+
+
+def lpdec_server_stats(server):
+    """(status, device bytes held, arena size, arena bytes in use, outstanding
+    tickets)."""
+    hb, ab, used = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    out = ctypes.c_int32()
+    rc = _load().lpdec_server_stats(server, ctypes.byref(hb), ctypes.byref(ab), ctypes.byref(used),
+                                    ctypes.byref(out))
+    return rc, hb.value, ab.value, used.value, out.value
+
+
+def region_bytes(n: int, m: int) -> int:
+    """Arena bytes one frame of a code with n bits and m checks holds in a
+    server (the layout lpdec_server_stats documents)."""
+    up = lambda v, a: (v + a - 1) // a * a  # noqa: E731
+    u = up(8 * n, 16)
+    hard = up(u + 8 * n, 16)
+    mask = up(hard + n, 16)
+    cert = up(mask + 4 * m, 16)
+    st = up(cert + 4, 16)
+    return up(st + STATS_DTYPE.itemsize, 256)
 
 
 def lpdec_server_destroy(server):
@@ -438,35 +470,83 @@ def lpdec_server_destroy(server):
 
 
 class Server:
-    """Submit frames as they arrive, poll their results (a thin wrapper of
-    the C serving entry points)."""
+    """Submit frames of several codes as they arrive, poll their results (a
+    thin wrapper of the C serving entry points; it owns a context holding
+    the codes' device copies)."""
 
-    def __init__(self, code, device: int = 0, params: lpdec_params | None = None,
-                 lanes: int = 2, batch: int = 512, max_pending: int = 1 << 16):
-        self.n = code.n
-        self.handle = lpdec_server_create(device, params, code, lanes, batch, max_pending)
+    def __init__(self, codes, device: int = 0, params: lpdec_params | None = None,
+                 hbm_budget_bytes: int = 0, max_pending: int = 1 << 16):
+        codes = list(codes) if isinstance(codes, (list, tuple)) else [codes]
+        self.ctx = lpdec_ctx_create(device, params)
+        self.handles, self.dims = [], {}
+        try:
+            for c in codes:
+                h = lpdec_code_create(self.ctx, int(c.m), int(c.n),
+                                      np.ascontiguousarray(c.row_ptr, dtype=np.int32),
+                                      np.ascontiguousarray(c.col_idx, dtype=np.int32))
+                self.handles.append(h)
+                self.dims[h] = (int(c.n), int(c.m))
+            self.handle = lpdec_server_create(device, params, self.handles, hbm_budget_bytes,
+                                              max_pending)
+        except Exception:
+            self._free_codes()
+            raise
+        self.code_of_ticket = {}
 
-    def submit(self, gamma) -> int:
-        rc, t = lpdec_submit(self.handle, gamma)
+    def _free_codes(self):
+        for h in self.handles:
+            lpdec_code_destroy(h)
+        self.handles = []
+        if self.ctx:
+            lpdec_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def submit(self, gamma, code: int = 0) -> int:
+        """Queues one frame of code index `code`; returns its ticket."""
+        h = self.handles[code]
+        rc, t = lpdec_submit(self.handle, h, gamma)
         _check(rc, "lpdec_submit")
+        self.code_of_ticket[t] = h
         return t
 
+    def try_submit(self, gamma, code: int = 0):
+        """(status, ticket) without raising (admission may refuse)."""
+        h = self.handles[code]
+        rc, t = lpdec_submit(self.handle, h, gamma)
+        if rc == LPDEC_OK:
+            self.code_of_ticket[t] = h
+        return rc, t
+
     def poll(self, ticket: int):
-        """(u, hard, cert, stats) once the frame is decoded, else None."""
-        u = np.empty(self.n, np.float64)
-        h = np.empty(self.n, np.uint8)
+        """(u, hard, cert, cut mask, stats) once the frame is decoded, else None."""
+        n, m = self.dims[self.code_of_ticket[ticket]]
+        u = np.empty(n, np.float64)
+        h = np.empty(n, np.uint8)
         c = np.zeros(1, np.int32)
+        mk = np.zeros(m, np.uint32)
         st = np.zeros(1, STATS_DTYPE)
-        rc = lpdec_poll(self.handle, ticket, u, h, c, st)
+        rc = lpdec_poll(self.handle, ticket, u, h, c, mk, st)
         if rc == LPDEC_ERR_PENDING:
             return None
         _check(rc, "lpdec_poll")
-        return u, h, int(c[0]), st[0]
+        self.code_of_ticket.pop(ticket, None)
+        return u, h, int(c[0]), mk, st[0]
+
+    def cancel(self, ticket: int):
+        _check(lpdec_cancel(self.handle, ticket), "lpdec_cancel")
+        self.code_of_ticket.pop(ticket, None)
+
+    def stats(self):
+        """(device bytes held, arena size, arena bytes in use, outstanding)."""
+        rc, hb, ab, used, out = lpdec_server_stats(self.handle)
+        _check(rc, "lpdec_server_stats")
+        return hb, ab, used, out
 
     def close(self):
-        if self.handle:
+        if getattr(self, "handle", None):
             lpdec_server_destroy(self.handle)
             self.handle = None
+        self._free_codes()
 
     def __enter__(self):
         return self

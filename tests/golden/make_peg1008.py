@@ -5,8 +5,8 @@ Workload (Sections III-D and VI-B: random (3,6) codes without 4-cycles,
 all-zero codeword, BPSK over AWGN): the (3,6) PEG-style code n = 1008,
 m = 504 (seed 0), frames 0..63 of the seed-0 pool at each Eb/N0 in
 {1.5, 2.0, 2.5, 3.0} dB, plus frames 6188 and 8718 at 2.0 dB, two frames
-whose MALP-A cost stops rising (Theorem 2(b) fails there) so that they
-continue as ALP (Algorithm 1).
+whose MALP-A cost stopped rising when LP vertices were accepted without a
+dual certificate (they reach the full-LP optimum with certified LPs).
 
 Every value comes from oracle.decode (FP64, dense Newton solves) with the
 default parameters; nothing is read from the CUDA path. Per frame it

@@ -110,20 +110,27 @@ def test_server_reports_missing_device_and_null_handles(lib):
     code = named_code("gallager_120")
     if not torch.cuda.is_available():
         with pytest.raises(L.LpdecError) as e:
-            L.Server(code)
+            L.Server([code])
         assert e.value.code == L.LPDEC_ERR_NO_DEVICE
-    assert lib.lpdec_submit(None, None, None) == L.LPDEC_ERR_INVALID_ARG
-    assert lib.lpdec_poll(None, 0, None, None, None, None) == L.LPDEC_ERR_INVALID_ARG
+    assert lib.lpdec_submit(None, None, None, None) == L.LPDEC_ERR_INVALID_ARG
+    assert lib.lpdec_poll(None, 0, None, None, None, None, None) == L.LPDEC_ERR_INVALID_ARG
+    assert lib.lpdec_cancel(None, 0) == L.LPDEC_ERR_INVALID_ARG
+    assert lib.lpdec_server_stats(None, None, None, None, None) == L.LPDEC_ERR_INVALID_ARG
     assert lib.lpdec_server_destroy(None) == L.LPDEC_ERR_INVALID_ARG
-    bad = L.lpdec_params()
-    L.library().lpdec_default_params(ctypes.byref(bad))
     out = ctypes.c_void_p()
-    rp = np.array([0, 2], np.int32)
-    ci = np.array([0, 1], np.int32)
-    for lanes, batch, pend in ((0, 4, 4), (17, 4, 4), (1, 0, 4), (1, 4, 0)):
-        rc = lib.lpdec_server_create(0, ctypes.byref(bad), 1, 2, rp.ctypes.data, ci.ctypes.data,
-                                     lanes, batch, pend, ctypes.byref(out))
+    for ncodes, pending in ((0, 4), (1, 0), (1, 1 << 21)):
+        rc = lib.lpdec_server_create(0, None, ncodes, None, 0, pending, ctypes.byref(out))
         assert rc == L.LPDEC_ERR_INVALID_ARG
+
+
+def test_server_region_bytes():
+    """The arena region of one frame: LLRs, u, hard, cut mask, cert and
+    stats, 16-byte aligned parts, 256-byte multiple."""
+    assert L.region_bytes(1008, 504) == 1024 * 19
+    for n, m in ((120, 60), (1008, 504), (4032, 2016), (7, 3)):
+        b = L.region_bytes(n, m)
+        assert b % 256 == 0 and 17 * n + 4 * m + 4 + L.STATS_DTYPE.itemsize <= b
+        assert b < 17 * n + 4 * m + 4 + L.STATS_DTYPE.itemsize + 64 + 256
 
 
 def test_largest_decodable_sizes(lib):

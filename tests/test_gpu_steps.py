@@ -191,7 +191,7 @@ def test_lp_solve_matches_oracle_vertex(dec120):
     prm = OracleParams()
     for f, lp in enumerate(lps):
         r = oipm.solve(lp.A, lp.b, lp.c, prm)
-        xv, ok = overtex.recover(lp.A, lp.b, lp.c, r.x, r.z)
+        xv, ok = overtex.recover(lp.A, lp.b, lp.c, r.x, r.z, r.y)
         assert ok and st["status"][f] == 0 and st["vertex_failures"][f] == 0
         assert np.max(np.abs(x[f, :lp.q] - xv)) < 1e-9, f
         assert abs(st["objective"][f] - lp.objective_u(xv, g[f])) <= 1e-9 * (1 + abs(st["objective"][f]))
