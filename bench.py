@@ -83,6 +83,13 @@ def parse_args():
                     help="seconds of the plain one-frame-per-launch arm (0 = skip)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per k_decode launch from an ncu capture of this build")
+    ap.add_argument("--workload", choices=["c2", "c4", "c5"], default="c2",
+                    help="c2: the batched decode of the metric (default); c4 / c5: serving with "
+                         "Poisson arrivals of mixed-length frames (one JSON line of their own)")
+    ap.add_argument("--serve-frames", type=int, default=3000,
+                    help="frames per load level of the serving workloads")
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0,
+                    help="HBM admission budget of the serving workloads")
     return ap.parse_args()
 
 
@@ -411,6 +418,131 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+# Serving workloads: Poisson arrivals of frames of several codes
+# ---------------------------------------------------------------------------
+
+SERVING = {
+    "c4": {"codes": ["gallager_504", "peg_1008", "gallager_2016", "gallager_4032"],
+           "ebn0": (1.5, 3.0),
+           "what": "(3,6)-regular codes n in {504, 1008, 2016, 4032} in equal proportion, "
+                   "Eb/N0 uniform in [1.5, 3.0] dB"},
+    "c5": {"codes": ["gallager330_8000", "irregular_4000"], "ebn0": (2.5, 4.5),
+           "what": "(3,30)-regular n=8000 (rate 0.9) and irregular lambda(x)=0.25x+0.3x^2+0.45x^7, "
+                   "check degree 8, n=4000, in equal proportion, Eb/N0 uniform in [2.5, 4.5] dB"},
+}
+
+
+def serving_frames(spec, codes, count, offset, seed=SEED):
+    """Frame k: its code (uniform over the workload's codes) and LLRs at an
+    Eb/N0 drawn uniformly from the workload's range, from seeded streams."""
+    import numpy as np
+    from synth import awgn_llr_frames
+    out = []
+    lo, hi = spec["ebn0"]
+    for k in range(offset, offset + count):
+        rng = np.random.default_rng([seed, 7, k])
+        ci = int(rng.integers(len(codes)))
+        eb = float(rng.uniform(lo, hi))
+        c = codes[ci]
+        out.append((ci, awgn_llr_frames(c.n, c.design_rate, eb, seed, [k])[0]))
+    return out
+
+
+L_OUT_OF_BUDGET = -2   # lpdec.h LPDEC_ERR_OUT_OF_BUDGET
+
+
+def serve_run(srv, frames, rate=None):
+    """Submits frames (as fast as admission allows if rate is None, else at
+    Poisson arrival times of that rate), polls them; returns (elapsed,
+    latencies in s, statuses)."""
+    import numpy as np
+    import time as _t
+    n = len(frames)
+    if rate is None:
+        arrive = np.zeros(n)
+    else:
+        arrive = np.cumsum(np.random.default_rng([SEED, 11, n]).exponential(1.0 / rate, n))
+    lat = np.zeros(n)
+    status = np.zeros(n, np.int32)
+    pending = {}
+    k = 0
+    t0 = _t.perf_counter()
+    while k < n or pending:
+        now = _t.perf_counter() - t0
+        progressed = False
+        while k < n and arrive[k] <= now:
+            rc, t = srv.try_submit(frames[k][1], code=frames[k][0])
+            if rc == L_OUT_OF_BUDGET:
+                break                       # admission refused: poll, then retry
+            if rc != 0:
+                raise RuntimeError(f"submit failed: {rc}")
+            pending[t] = (k, max(arrive[k], 0.0) if rate is not None else now)
+            k += 1
+            progressed = True
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                kk, ta = pending.pop(t)
+                lat[kk] = _t.perf_counter() - t0 - ta
+                status[kk] = r[4]["status"]
+                progressed = True
+        if not progressed:
+            _t.sleep(0.0002)
+    return _t.perf_counter() - t0, lat, status
+
+
+def run_serving(args):
+    import numpy as np
+    import torch
+    from paper_0902_0657_gb300 import build as B
+    from paper_0902_0657_gb300 import lpdec as L
+    from synth import named_code
+    B.build()
+    torch.cuda.set_device(0)
+    spec = SERVING[args.workload]
+    codes = [named_code(nm) for nm in spec["codes"]]
+    prm = L.lpdec_default_params()
+    prm.precision = {"fp64": L.LPDEC_FP64, "mixed": L.LPDEC_MIXED, "m32": L.LPDEC_M32}[args.precision]
+    N = args.serve_frames
+    budget = int(args.serve_budget_gb * (1 << 30))
+    levels = {}
+    with L.Server(codes, params=prm, hbm_budget_bytes=budget, max_pending=1 << 14) as srv:
+        warm = serving_frames(spec, codes, 64, 10 ** 6)
+        serve_run(srv, warm)
+        sat_frames = serving_frames(spec, codes, N, 0)
+        el, lat, st = serve_run(srv, sat_frames)
+        sat = N / el
+        levels["saturated"] = {"frames_per_s": sat, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                               "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                               "p99.9_ms": 1e3 * float(np.percentile(lat, 99.9)),
+                               "frames_ok": int((st == 0).sum())}
+        for i, load in enumerate((0.5, 0.8, 0.95)):
+            fr = serving_frames(spec, codes, N, (i + 1) * N)
+            el, lat, st = serve_run(srv, fr, rate=load * sat)
+            levels[f"poisson_{int(load * 100)}pct"] = {
+                "offered_frames_per_s": load * sat, "frames_per_s": N / el,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "p99.9_ms": 1e3 * float(np.percentile(lat, 99.9)),
+                "frames_ok": int((st == 0).sum())}
+        hbm, arena, used, out = srv.stats()
+    line = {
+        "metric": f"served LP-decoded frames/s, {args.workload} mixed lengths; p50/p99/p99.9 latency",
+        "value": sat, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {spec['what']}; {N} frames per load level "
+                               f"(the configuration's frame count scaled down to bound the run)",
+                   "codes": spec["codes"], "hbm_budget_gb": args.serve_budget_gb,
+                   "server_device_bytes": hbm, "precision": args.precision},
+        "levels": levels,
+        "latency": "host clock from a frame's arrival (its scheduled Poisson time) to the poll "
+                   "that returns its result",
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the CPU oracle on the host cores
 # ---------------------------------------------------------------------------
 
@@ -446,6 +578,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in SERVING:
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -318,6 +318,24 @@ int32_t lpdec_pcg_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes
                          const double* d_w, double* d_dy, int32_t* d_iters,
                          void* stream);
 
+/* Diagnostic PCG (Algorithm 4, FP64, one run from dy = 0, no refinement)
+ * for the preconditioner study of Section VI-B and the spectral diagnostics
+ * of its closing remarks: the LP given by (gamma, in_lp, mask), weights and
+ * D^2 = d2[nframes x (n+m)], right side w[nframes x m], preconditioned by
+ * the context's triangular set (lpdec_params.precond) or, with identity != 0,
+ * not at all (plain CG). Runs until ||r|| < tol ||w|| or max_hist
+ * iterations; writes dy[nframes x m], iters[nframes] and, per frame and
+ * iteration k < max_hist, hist[(f * max_hist + k) * 3 ...] = ||r_k|| / ||w||,
+ * alpha_k, nu_k (zeros past the last iteration). The coefficients define
+ * the Lanczos tridiagonal of the preconditioned operator (diagonal
+ * 1/alpha_k + nu_{k-1}/alpha_{k-1}, off-diagonal sqrt(nu_k)/alpha_k), whose
+ * extreme eigenvalues estimate its condition number. */
+int32_t lpdec_pcg_trace_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                               const double* d_gamma, const uint8_t* d_in_lp,
+                               const uint32_t* d_mask, const double* d_d2, const double* d_w,
+                               int32_t identity, double tol, int32_t max_hist, double* d_dy,
+                               int32_t* d_iters, double* d_hist, void* stream);
+
 /* Solves one LP (Section IV-B interior-point method + optimal-vertex
  * recovery) given by (gamma, in_lp, mask): x[nframes x (n+m)] out (the
  * recovered vertex, slacks at n..n+p-1), stats[nframes] out
@@ -327,11 +345,15 @@ int32_t lpdec_lp_solve_device(lpdec_ctx* ctx, const lpdec_code* code,
                               const uint8_t* d_in_lp, const uint32_t* d_mask,
                               double* d_x, lpdec_stats* d_stats, void* stream);
 
-/* Diagnostic form of lpdec_lp_solve_device: also writes, per frame and per
- * interior-point iteration k < max_trace, 8 doubles to
- * trace[(f * max_trace + k) * 8 ...]: relative gap, relative primal and dual
- * infeasibility, PCG iterations, final PCG relative residual, beta_P,
- * beta_D, and the deepest triangular-solve level schedule. */
+/* Diagnostic form of lpdec_lp_solve_device (one interior-point run, without
+ * the refinement of an uncertified vertex): also writes, per frame and per
+ * interior-point iteration k < max_trace, 10 doubles to
+ * trace[(f * max_trace + k) * 10 ...]: relative gap, relative primal and
+ * dual infeasibility, PCG iterations, final PCG relative residual, beta_P,
+ * beta_D, the deepest triangular-solve level schedule, and the smallest and
+ * largest eigenvalue of the Lanczos tridiagonal of the Newton solve's first
+ * PCG round (its first 64 CG coefficients): an estimate of the spectrum of
+ * M^-1 Q, the preconditioned normal matrix (Section VI). */
 int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code,
                                     int32_t nframes, const double* d_gamma,
                                     const uint8_t* d_in_lp, const uint32_t* d_mask,

@@ -36,6 +36,38 @@ def parity_inequalities(code):
     return np.asarray(rows), np.asarray(rhs)
 
 
+def parity_inequalities_sparse(code):
+    """The rows of ``parity_inequalities`` as a scipy CSR matrix (codes whose
+    dense inequality matrix would not fit memory, e.g. n = 16000)."""
+    import scipy.sparse as sp
+    indptr, indices, data, rhs = [0], [], [], []
+    for j in range(code.m):
+        nbrs = code.row(j)
+        d = nbrs.size
+        for size in range(1, d + 1, 2):
+            for V in itertools.combinations(range(d), size):
+                sgn = -np.ones(d)
+                sgn[list(V)] = 1.0
+                indices.extend(nbrs.tolist())
+                data.extend(sgn.tolist())
+                indptr.append(len(indices))
+                rhs.append(size - 1.0)
+    A = sp.csr_matrix((np.asarray(data), np.asarray(indices), np.asarray(indptr)),
+                      shape=(len(rhs), code.n))
+    return A, np.asarray(rhs)
+
+
+def lp_decode_sparse(code, gamma):
+    """Full LP decoding (Eq. 7) with a sparse constraint matrix. Returns
+    (u, objective)."""
+    A, b = parity_inequalities_sparse(code)
+    res = linprog(np.asarray(gamma, dtype=np.float64), A_ub=A, b_ub=b,
+                  bounds=(0.0, 1.0), method="highs-ds")
+    if res.status != 0:
+        raise RuntimeError(f"linprog failed: {res.message}")
+    return res.x, float(res.fun)
+
+
 def lp_decode(code, gamma):
     """Full LP decoding (Eq. 7). Returns (u, objective)."""
     A, b = parity_inequalities(code)

@@ -211,12 +211,54 @@ k_pcg(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in
     }
 }
 
+// Diagnostic PCG with the context's preconditioner (or plain CG): residual
+// and coefficient history per frame (pcg_traced).
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_pcg_trace(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
+            const uint32_t* mask, const double* d2, const double* wv, double* dy, int32_t* iters,
+            double* hist, int max_hist, int identity, double tol, int nframes, int* counter,
+            char* gscratch) {
+    KERNEL_PROLOGUE
+    const CodeView C = bind_code<T>(C0, W);
+    const int qm = C.n + C.m;
+    for (;;) {
+        int f = next_frame(B, counter, &ks.next);
+        if (f >= nframes) break;
+        load_lp_state<T>(B, C, W, gamma + (size_t)f * C.n, in_lp + (size_t)f * C.m,
+                         mask + (size_t)f * C.m);
+        Frame F{0, C.n, 0.0, 0.0, 0};
+        lp_build<T>(B, C, W, F, ks.shscan, false, C.pmax, C.eamax);
+        for (int i = B.tid; i < F.q; i += B.nt) W.d2[i] = d2[(size_t)f * qm + i];
+        for (int r = B.tid; r < F.p; r += B.nt) W.r[r] = (T)wv[(size_t)f * C.m + r];
+        __syncthreads();
+        Levels Lv{-1, -1};
+        if (!identity)
+            Lv = select_mts<T>(B, C, W, F, W.d2,
+                               P.precond == LPDEC_MTS_ADAPTIVE ? LPDEC_MTS_COLUMN : P.precond);
+        for (int i = B.tid; i < F.q; i += B.nt) W.d2t[i] = (T)W.d2[i];
+        for (int r = B.tid; r < F.p; r += B.nt) {
+            const int pc = identity ? 0 : W.pivcol[r];
+            W.invd2p[r] = identity ? T(1) : (T)(1.0 / W.d2[pc]);
+        }
+        for (int r = B.tid; r < F.p; r += B.nt) W.r[r] = (T)wv[(size_t)f * C.m + r];
+        for (int k = B.tid; k < 3 * max_hist; k += B.nt) hist[(size_t)f * 3 * max_hist + k] = 0.0;
+        __syncthreads();
+        int it = pcg_traced<T>(B, C, W, F, Lv, identity != 0, tol, max_hist,
+                               hist + (size_t)f * 3 * max_hist);
+        for (int r = B.tid; r < C.m; r += B.nt) dy[(size_t)f * C.m + r] = r < F.p ? (double)W.xs[r] : 0.0;
+        if (B.tid == 0) iters[f] = it;
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512)
 k_lp_solve(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in_lp,
            const uint32_t* mask, double* xo, lpdec_stats* stats, int nframes, int* counter,
            char* gscratch, double* trace, int max_trace) {
     KERNEL_PROLOGUE
+    double* const W0lz = reinterpret_cast<double*>(ws_ptr(L, G_LZ, smem, gscratch + (size_t)blockIdx.x * L.stride));
     const CodeView C = bind_code<T>(C0, W);
     const int qm = C.n + C.m;
     for (;;) {
@@ -231,8 +273,10 @@ k_lp_solve(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_
             IpmOut io;
             bool solved;
             if (trace) {   // one run, traced (no refinement)
-                io = ipm_solve<T>(B, C, W, F, P, g, 0, trace + (size_t)f * 8 * max_trace,
+                W.lz = W0lz;
+                io = ipm_solve<T>(B, C, W, F, P, g, 0, trace + (size_t)f * kTrace * max_trace,
                                   max_trace);
+                W.lz = nullptr;
                 int ok = io.certified || certify<T>(B, C, W, F, g);
                 if (!ok) st.vertex_failures = vertex_recover<T>(B, C, W, F, g);
                 solved = io.converged || ok;
@@ -427,7 +471,7 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
         {G_P64, real_bytes < 8 ? D * vec_elems(n, pm) : 16, 2},
         {G_QD, dense_rows > 0 ? D * (size_t)dense_rows * dense_rows : 16, 2},
         {G_CCHK2, H * P, 2}, {G_CMASK2, I * P, 2}, {G_CRPTR2, I * ((size_t)m + 1), 2},
-        {G_GAM, D * (size_t)n, 2},
+        {G_GAM, D * (size_t)n, 2}, {G_LZ, D * (2 * (size_t)kLz + 2), 2},
     };
     Layout L{};
     size_t s = 0, g = 0;
@@ -457,8 +501,10 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
 }
 
 // Rows of the dense fallback's matrix: the main capacity and a quarter more
-// (frames continued as ALP), at most 2048.
+// (frames continued as ALP); off for codes whose main capacity exceeds 2048
+// rows (its matrix would not be worth its memory).
 int dense_rows_for(const Dims& d) {
+    if (d.pmax > kDenseMaxRows) return 0;
     return std::min({d.pmax + d.pmax / 4, std::max(d.pwide, d.pmax), kDenseMaxRows});
 }
 
@@ -1107,6 +1153,31 @@ int32_t lpdec_pcg_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes
         k_pcg<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
         view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_dy,
         d_iters, nframes, ctx->counter, ctx->gscratch);
+    CK(cudaGetLastError());
+    return LPDEC_OK;
+}
+
+int32_t lpdec_pcg_trace_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                               const double* d_gamma, const uint8_t* d_in_lp,
+                               const uint32_t* d_mask, const double* d_d2, const double* d_w,
+                               int32_t identity, double tol, int32_t max_hist, double* d_dy,
+                               int32_t* d_iters, double* d_hist, void* stream) {
+    int32_t rc = check_ctx_code(ctx, code);
+    if (rc) return rc;
+    if (nframes < 0 || max_hist < 1 || !(tol > 0.0) ||
+        (nframes > 0 && (!d_gamma || !d_in_lp || !d_mask || !d_d2 || !d_w || !d_dy || !d_iters ||
+                         !d_hist)))
+        return LPDEC_ERR_INVALID_ARG;
+    if (nframes == 0) return LPDEC_OK;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    Launch ln;
+    rc = plan(ctx, code, nframes, k_pcg_trace<double>, 8, &ln);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
+    k_pcg_trace<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
+        view_of(code, ctx->prm), to_dev(ctx->prm), ln.L, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_dy,
+        d_iters, d_hist, max_hist, identity ? 1 : 0, tol, nframes, ctx->counter, ctx->gscratch);
     CK(cudaGetLastError());
     return LPDEC_OK;
 }

@@ -81,6 +81,8 @@ enum Arr {
     // the CTA's copy of the frame's LLRs (serving: read from the shared arena
     // once, past the SM's L1)
     G_GAM,
+    // CG coefficients of the first PCG round of a traced Newton solve
+    G_LZ,
     A_COUNT
 };
 
@@ -114,7 +116,7 @@ struct Layout {
 __host__ __device__ constexpr bool row_sized(int a) {
     return !(a == S_FLAGS || a == S_MASK || a == S_FLIP || a == S_HPTR || a == S_VPTR ||
              a == S_CPTR || a == S_CRPTR || a == G_U || a == G_T64 || a == G_QD ||
-             a == G_CRPTR2 || a == G_GAM);
+             a == G_CRPTR2 || a == G_GAM || a == G_LZ);
 }
 
 template <typename T>
@@ -135,6 +137,7 @@ struct WS {
     double *vx, *v1, *v2, *v3, *v4, *vr1, *vr2, *p64;
     double* qd;   // dense Cholesky factor (column-major p x p), null when off
     double* gam;  // private copy of the frame's LLRs (serving)
+    double* lz;   // CG coefficient record of traced solves (null when not tracing)
     uint16_t* cchk2;
     uint32_t *cmask2, *crptr2;
     int cap_n, cap_p;   // capacities the sub-arrays were sliced with
@@ -188,7 +191,9 @@ __device__ inline void point_ws(WS<T>& w, const Layout& L, char* smem, char* gws
     P_(uint16_t, cchk2, G_CCHK2); P_(uint32_t, cmask2, G_CMASK2);
     P_(uint32_t, crptr2, G_CRPTR2);
     P_(double, gam, G_GAM);
+    P_(double, lz, G_LZ);
 #undef P_
+    if (!only_rows) w.lz = nullptr;   // set by the traced entry point only
     if (!only_rows) {
         if (!L.dense) w.qd = nullptr;
         w.dense_p = (int)L.dense;
@@ -232,7 +237,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W) {
     v.x = W.x; v.zz = W.zz; v.rc = W.rc; v.d2 = W.d2; v.y = W.y; v.b = W.b; v.w = W.w;
     v.dy = W.dy; v.r64 = W.r64; v.u = W.u; v.t64 = W.t64;
     v.vx = W.vx; v.v1 = W.v1; v.v2 = W.v2; v.v3 = W.v3; v.v4 = W.v4; v.vr1 = W.vr1;
-    v.vr2 = W.vr2; v.p64 = W.p64; v.qd = W.qd; v.gam = W.gam;
+    v.vr2 = W.vr2; v.p64 = W.p64; v.qd = W.qd; v.gam = W.gam; v.lz = W.lz;
     v.cchk2 = W.cchk2; v.cmask2 = W.cmask2; v.crptr2 = W.crptr2;
     return v;
 }
@@ -752,7 +757,7 @@ __device__ inline void back_levels(Blk& B, WS<T>& W, int p) {
 }
 
 template <typename T>
-__device__ __noinline__ Levels mts_select(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ Levels mts_select(Blk& B, const CodeView C, WS<T> W, const Frame& F,
                                     const double* wt, int /*q2*/) {
     const int n = C.n, p = F.p, q = F.q;
     for (int i = B.tid; i < q; i += B.nt) {
@@ -859,7 +864,7 @@ __device__ __forceinline__ void bit_clear(uint32_t* bm, int i) { atomicAnd(&bm[i
 // computed.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __noinline__ Levels mts_rowwise(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ Levels mts_rowwise(Blk& B, const CodeView C, WS<T> W, const Frame& F,
                                      const double* wt) {
     const int n = C.n, p = F.p, q = F.q;
     uint16_t* rowdeg = W.lb;
@@ -1047,7 +1052,7 @@ __device__ inline int peel_set(Blk& B, WS<T>& W, int n, int p, int s, uint16_t s
 }
 
 template <typename T>
-__device__ __noinline__ Levels mts_incremental(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ Levels mts_incremental(Blk& B, const CodeView C, WS<T> W, const Frame& F,
                                          const double* wt) {
     const int n = C.n, p = F.p, q = F.q;
     uint16_t* rowcnt = W.lb;
@@ -1337,6 +1342,60 @@ __device__ inline double spmv_Q(Blk& B, const CodeView& C, WS<T>& W, const Frame
     return bsum(B, hl);
 }
 
+// Record of CG coefficients for the Lanczos estimate of a traced solve:
+// lz[2k] = alpha_k, lz[2k+1] = nu_k (k < kLz), lz[2 kLz] = count,
+// lz[2 kLz + 1] = 1 once the first PCG round has ended.
+constexpr int kLz = 64;
+__device__ __forceinline__ void lz_record(double* lz, double alpha, double nu) {
+    const int k = (int)lz[2 * kLz];
+    if (lz[2 * kLz + 1] == 0.0 && k < kLz) {
+        lz[2 * k] = alpha;
+        lz[2 * k + 1] = nu;
+        lz[2 * kLz] = k + 1;
+    }
+}
+
+// Extreme eigenvalues of the Lanczos tridiagonal of the recorded CG
+// coefficients (diagonal 1/alpha_k + nu_{k-1}/alpha_{k-1}, off-diagonal
+// sqrt(nu_k)/alpha_k), by bisection on Sturm counts inside the Gershgorin
+// interval (one thread).
+__device__ inline void lz_extremes(const double* lz, double* lo, double* hi) {
+    const int k = (int)lz[2 * kLz];
+    *lo = *hi = NAN;
+    if (k < 1) return;
+    double d[kLz], e[kLz];
+    double gl = INFINITY, gh = -INFINITY;
+    for (int j = 0; j < k; ++j) {
+        d[j] = 1.0 / lz[2 * j] + (j > 0 ? lz[2 * j - 1] / lz[2 * j - 2] : 0.0);
+        e[j] = j + 1 < k ? sqrt(fmax(lz[2 * j + 1], 0.0)) / lz[2 * j] : 0.0;
+    }
+    for (int j = 0; j < k; ++j) {
+        const double rad = fabs(e[j]) + (j > 0 ? fabs(e[j - 1]) : 0.0);
+        gl = fmin(gl, d[j] - rad);
+        gh = fmax(gh, d[j] + rad);
+    }
+    auto below = [&](double x) {   // eigenvalues < x
+        int c = 0;
+        double q = d[0] - x;
+        if (q < 0.0) ++c;
+        for (int j = 1; j < k; ++j) {
+            const double qq = (q == 0.0) ? 1e-300 : q;
+            q = d[j] - x - e[j - 1] * e[j - 1] / qq;
+            if (q < 0.0) ++c;
+        }
+        return c;
+    };
+    for (int which = 0; which < 2; ++which) {   // 0: smallest, 1: largest
+        double a = gl, b = gh;
+        for (int t = 0; t < 200 && b - a > 1e-14 * fmax(fabs(a), fabs(b)); ++t) {
+            const double mid = 0.5 * (a + b);
+            const bool left = which == 0 ? below(mid) >= 1 : below(mid) >= k;
+            if (left) b = mid; else a = mid;
+        }
+        if (which == 0) *lo = 0.5 * (a + b); else *hi = 0.5 * (a + b);
+    }
+}
+
 // PCG (Algorithm 4) in type T on Q xs = r (right side in W.r, overwritten by
 // the residual), x0 = 0, stopping when ||r||_2 < tol ||rhs||_2 or after
 // max_it iterations. Dot products accumulate in FP64.
@@ -1383,13 +1442,79 @@ __device__ inline int pcg(Blk& B, const CodeView& C, WS<T>& W, const Frame& F, c
         }
         s = bsum2(B, zr_l, rr_l);
         T nu = (T)(s.x / zr);
+        if (W.lz && B.tid == 0) lz_record(W.lz, (double)alpha, s.x / zr);
         zr = s.x;
         rr = s.y;
         for (int r = B.tid; r < p; r += B.nt) W.h[r] = W.z[r] + nu * W.h[r];
         __syncthreads();
         ++it;
     }
+    if (W.lz && B.tid == 0) W.lz[2 * kLz + 1] = 1.0;   // later rounds are not recorded
     *relres = isfinite(rr) ? sqrt(rr) / rn0 : INFINITY;
+    return it;
+}
+
+// Diagnostic PCG (Algorithm 4) in FP64 on Q xs = r (right side in W.r),
+// x0 = 0, that records per iteration k < max_hist: hist[3k] = ||r_k|| /
+// ||r_0||, hist[3k+1] = alpha_k, hist[3k+2] = nu_k. The coefficients give the
+// Lanczos tridiagonal of the preconditioned operator M^-1 Q, whose extreme
+// eigenvalues estimate its condition number. identity = true runs plain CG
+// (M = I). Stops at ||r|| < tol ||r_0|| or after max_hist iterations.
+template <typename T>
+__device__ inline int pcg_traced(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+                                 const Levels& L, bool identity, double tol, int max_hist,
+                                 double* hist) {
+    const int p = F.p;
+    auto apply_m = [&]() {
+        if (identity) {
+            for (int r = B.tid; r < p; r += B.nt) W.z[r] = W.r[r];
+            __syncthreads();
+        } else {
+            msolve<T>(B, C, W, L, W.r, W.z, T(0));
+        }
+    };
+    for (int r = B.tid; r < p; r += B.nt) W.xs[r] = T(0);
+    __syncthreads();
+    apply_m();
+    double zr0 = 0.0, rr0 = 0.0;
+    for (int r = B.tid; r < p; r += B.nt) {
+        W.h[r] = W.z[r];
+        zr0 += (double)W.z[r] * (double)W.r[r];
+        rr0 += (double)W.r[r] * (double)W.r[r];
+    }
+    double2 s = bsum2(B, zr0, rr0);
+    double zr = s.x, rr = s.y;
+    const double rn0 = sqrt(rr);
+    if (rn0 == 0.0) return 0;
+    int it = 0;
+    while (sqrt(rr) >= tol * rn0 && it < max_hist) {
+        double hl = spmv_Q<T>(B, C, W, F, W.h, W.l);
+        if (!(hl > 0.0) || !isfinite(hl)) break;
+        const double alpha = zr / hl;
+        for (int r = B.tid; r < p; r += B.nt) {
+            W.r[r] -= (T)alpha * W.l[r];
+            W.xs[r] += (T)alpha * W.h[r];
+        }
+        __syncthreads();
+        apply_m();
+        double zr_l = 0.0, rr_l = 0.0;
+        for (int r = B.tid; r < p; r += B.nt) {
+            zr_l += (double)W.z[r] * (double)W.r[r];
+            rr_l += (double)W.r[r] * (double)W.r[r];
+        }
+        s = bsum2(B, zr_l, rr_l);
+        const double nu = s.x / zr;
+        zr = s.x;
+        rr = s.y;
+        for (int r = B.tid; r < p; r += B.nt) W.h[r] = W.z[r] + (T)nu * W.h[r];
+        if (B.tid == 0) {
+            hist[3 * it] = sqrt(rr) / rn0;
+            hist[3 * it + 1] = alpha;
+            hist[3 * it + 2] = nu;
+        }
+        __syncthreads();
+        ++it;
+    }
     return it;
 }
 
@@ -1535,7 +1660,7 @@ constexpr double kPivotTiny = 1e-13;
 constexpr double kPivotHuge = 1e64;
 
 template <typename T>
-__device__ __noinline__ bool dense_newton(Blk& B, const CodeView& C, WS<T>& W, const Frame& F) {
+__device__ __noinline__ bool dense_newton(Blk& B, const CodeView C, WS<T> W, const Frame& F) {
     const int n = C.n, p = F.p;
     double* Lm = W.qd;
     const size_t pp = (size_t)p * p;
@@ -1604,7 +1729,7 @@ __device__ __noinline__ bool dense_newton(Blk& B, const CodeView& C, WS<T>& W, c
 }
 
 template <typename T>
-__device__ __noinline__ NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                          const Levels& L, const DevParams& P, double tol,
                                          int max_it, bool& force64, bool& force_dense) {
     const int p = F.p;
@@ -1725,7 +1850,7 @@ __device__ __forceinline__ double cost_of(const double* gamma, int n, int i) {
 }
 
 template <typename T>
-__device__ __noinline__ int certify(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ int certify(Blk& B, const CodeView C, WS<T> W, const Frame& F,
                               const double* gamma) {
     const int n = C.n, p = F.p, q = F.q;
     double nbasic = 0.0, cmax = 0.0;
@@ -1855,7 +1980,7 @@ __device__ __noinline__ int certify(Blk& B, const CodeView& C, WS<T>& W, const F
 // and dual feasible and complementary, so x^ is optimal (and, the optimum
 // being unique, the vertex the oracle reaches). On success x := x^.
 template <typename T>
-__device__ __noinline__ int certify_basis(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ int certify_basis(Blk& B, const CodeView C, WS<T> W, const Frame& F,
                                     const Levels& L, const double* gamma) {
     const int n = C.n, p = F.p, q = F.q;
     WS<double> D = fp64_view<T>(W);
@@ -1905,6 +2030,9 @@ __device__ __noinline__ int certify_basis(Blk& B, const CodeView& C, WS<T>& W, c
 // ---------------------------------------------------------------------------
 // a3 + a6: infeasible primal-dual path-following method (Section IV-B)
 // ---------------------------------------------------------------------------
+// Doubles per interior-point iteration in a trace (lpdec_lp_solve_trace_device).
+constexpr int kTrace = 10;
+
 struct IpmOut {
     int iters, pcg_iters, pcg_iters64, converged, certified, max_levels, dense;
     double flops, bytes;
@@ -1913,7 +2041,7 @@ struct IpmOut {
 // trace (optional): per iteration 8 doubles {gap, feas_p, feas_d, PCG
 // iterations, Newton relative residual, beta_P, beta_D, levels}
 template <typename T>
-__device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Frame& F,
+__device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Frame& F,
                                    const DevParams& P, const double* gamma, int q2,
                                    double* trace = nullptr, int max_trace = 0) {
     const int n = C.n, p = F.p, q = F.q;
@@ -2016,6 +2144,8 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Fr
         }
         __syncthreads();
         const double tol = fmax(P.tol_pcg, fmin(1e-3, P.pcg_gap_factor * g_rel));
+        if (W.lz && B.tid == 0) { W.lz[2 * kLz] = 0.0; W.lz[2 * kLz + 1] = 0.0; }
+        __syncthreads();
         NewtonOut no = newton_solve<T>(B, C, W, F, L, P, tol, P.max_pcg, force64, force_dense);
         o.dense += no.dense;
         o.pcg_iters += no.iters;
@@ -2049,9 +2179,11 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Fr
         const double bp = fmin(1.0, P.eta * mn.x);
         const double bd = fmin(1.0, P.eta * mn.y);
         if (trace && it < max_trace && B.tid == 0) {
-            double* tr = trace + 8 * it;
+            double* tr = trace + kTrace * it;
             tr[0] = g_rel; tr[1] = fp; tr[2] = fd; tr[3] = no.iters; tr[4] = no.relres;
             tr[5] = bp; tr[6] = bd; tr[7] = max(L.nb, L.nf);
+            tr[8] = tr[9] = NAN;
+            if (W.lz) lz_extremes(W.lz, &tr[8], &tr[9]);
         }
         for (int i = B.tid; i < q; i += B.nt) {
             W.x[i] += bp * W.rc[i];
@@ -2074,7 +2206,7 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView& C, WS<T>& W, Fr
 // over rows (W.w, W.r64).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __noinline__ int vertex_recover(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
+__device__ __noinline__ int vertex_recover(Blk& B, const CodeView C, WS<T> W, const Frame& F,
                                      const double* gamma) {
     const int n = C.n, p = F.p, q = F.q;
     double* d = W.rc;

@@ -107,6 +107,8 @@ def _load():
     lib.lpdec_mts_select_device.argtypes = [P, P, i32, P, P, P, P, P, P, P]
     lib.lpdec_pcg_device.argtypes = [P, P, i32, P, P, P, P, P, P, P, P]
     lib.lpdec_lp_solve_device.argtypes = [P, P, i32, P, P, P, P, P, P]
+    lib.lpdec_pcg_trace_device.argtypes = [P, P, i32, P, P, P, P, P, i32, ctypes.c_double, i32,
+                                           P, P, P, P]
     lib.lpdec_lp_solve_trace_device.argtypes = [P, P, i32, P, P, P, P, P, P, i32, P]
     lib.lpdec_decode_batch_device_noalloc.argtypes = [P, ctypes.POINTER(lpdec_params), i32, P, P,
                                                       P, P, P, P, P]
@@ -126,6 +128,7 @@ def _load():
                  "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_frames",
                  "lpdec_decode_mixed_device", "lpdec_decode_batch_device",
                  "lpdec_cut_search_device", "lpdec_mts_select_device", "lpdec_pcg_device",
+                 "lpdec_pcg_trace_device",
                  "lpdec_lp_solve_device", "lpdec_lp_solve_trace_device",
                  "lpdec_decode_batch_device_noalloc"):
         getattr(lib, name).restype = i32
@@ -297,6 +300,31 @@ def lpdec_pcg_device(ctx, code, nframes, d_gamma, d_in_lp, d_mask, d_d2, d_w, d_
     return _load().lpdec_pcg_device(ctx, code, nframes, _dptr(d_gamma), _dptr(d_in_lp),
                                     _dptr(d_mask), _dptr(d_d2), _dptr(d_w), _dptr(d_dy),
                                     _dptr(d_iters), _stream(stream))
+
+
+def lpdec_pcg_trace_device(ctx, code, nframes, d_gamma, d_in_lp, d_mask, d_d2, d_w, identity,
+                           tol, max_hist, d_dy, d_iters, d_hist, stream=None) -> int:
+    return _load().lpdec_pcg_trace_device(ctx, code, nframes, _dptr(d_gamma), _dptr(d_in_lp),
+                                          _dptr(d_mask), _dptr(d_d2), _dptr(d_w), int(identity),
+                                          float(tol), max_hist, _dptr(d_dy), _dptr(d_iters),
+                                          _dptr(d_hist), _stream(stream))
+
+
+def lanczos_condition(hist_row, iters):
+    """Extreme eigenvalues (min, max) of the Lanczos tridiagonal that the CG
+    coefficients (alpha_k, nu_k) of one traced run define (host-side
+    post-processing of lpdec_pcg_trace_device's output)."""
+    k = int(iters)
+    if k < 1:
+        return float("nan"), float("nan")
+    a = np.asarray(hist_row).reshape(-1, 3)[:k, 1]
+    nu = np.asarray(hist_row).reshape(-1, 3)[:k, 2]
+    d = 1.0 / a
+    d[1:] += nu[:-1] / a[:-1]
+    e = np.sqrt(np.maximum(nu[:-1], 0.0)) / a[:-1]
+    T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[0]), float(ev[-1])
 
 
 def lpdec_lp_solve_device(ctx, code, nframes, d_gamma, d_in_lp, d_mask, d_x, d_stats,
@@ -519,6 +547,8 @@ class Server:
 
     def poll(self, ticket: int):
         """(u, hard, cert, cut mask, stats) once the frame is decoded, else None."""
+        if ticket not in self.code_of_ticket:   # never issued, polled or cancelled here
+            _check(lpdec_poll(self.handle, ticket), "lpdec_poll")
         n, m = self.dims[self.code_of_ticket[ticket]]
         u = np.empty(n, np.float64)
         h = np.empty(n, np.uint8)
