@@ -83,9 +83,14 @@ def parse_args():
                     help="seconds of the plain one-frame-per-launch arm (0 = skip)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per k_decode launch from an ncu capture of this build")
-    ap.add_argument("--workload", choices=["c2", "c4", "c5"], default="c2",
-                    help="c2: the batched decode of the metric (default); c4 / c5: serving with "
-                         "Poisson arrivals of mixed-length frames (one JSON line of their own)")
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
+                    help="c2: the batched decode of the metric (default); c3: the n=16000 "
+                         "precision study; c4 / c5: serving with Poisson arrivals of mixed-length "
+                         "frames (each prints one JSON line of its own)")
+    ap.add_argument("--c3-frames", type=int, default=32,
+                    help="frames of the n=16000 study (a subset of its 2000)")
+    ap.add_argument("--c3-oracle-frames", type=int, default=2,
+                    help="frames of the study checked against the full LP (HiGHS)")
     ap.add_argument("--serve-frames", type=int, default=3000,
                     help="frames per load level of the serving workloads")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0,
@@ -543,6 +548,125 @@ def run_serving(args):
 
 
 # ---------------------------------------------------------------------------
+# c3: precision study at n = 16000
+# ---------------------------------------------------------------------------
+
+def _full_lp_worker(args):
+    f, ebn0 = args
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    from oracle import feldman
+    from synth import awgn_llr_frames, named_code
+    c = named_code("gallager_16000")
+    g = awgn_llr_frames(c.n, c.design_rate, ebn0, SEED, [f])[0]
+    u, obj = feldman.lp_decode_sparse(c, g)
+    return f, obj
+
+
+def run_c3(args):
+    import numpy as np
+    import torch
+    from paper_0902_0657_gb300 import build as B
+    from paper_0902_0657_gb300 import lpdec as L
+    from synth import awgn_llr_frames, named_code
+    ebn0 = 1.8
+    cfut = None
+    pool = None
+    if args.c3_oracle_frames > 0:   # the full LP on host cores while the GPU runs
+        pool = mp.get_context("spawn").Pool(args.c3_oracle_frames)
+        cfut = pool.map_async(_full_lp_worker, [(f, ebn0) for f in range(args.c3_oracle_frames)])
+    B.build()
+    torch.cuda.set_device(0)
+    code = named_code("gallager_16000")
+    nf = args.c3_frames
+    G = awgn_llr_frames(code.n, code.design_rate, ebn0, SEED, range(nf))
+    modes = {}
+    outs = {}
+    for name, prec in (("fp64", L.LPDEC_FP64), ("mixed", L.LPDEC_MIXED)):
+        prm = L.lpdec_default_params()
+        prm.precision = prec
+        with L.Decoder(code, params=prm) as d:
+            d_g = torch.from_numpy(G).cuda()
+            d_u = torch.empty((nf, code.n), dtype=torch.float64, device="cuda")
+            d_h = torch.empty((nf, code.n), dtype=torch.uint8, device="cuda")
+            d_c = torch.empty(nf, dtype=torch.int32, device="cuda")
+            d_m = torch.empty((nf, code.m), dtype=torch.int32, device="cuda")
+            d_s = torch.empty(nf * L.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rc = L.lpdec_decode_batch_device(d.ctx, d.code, nf, d_g, d_u, d_h, d_c, d_m, d_s)
+            e1.record()
+            e1.synchronize()
+            if rc != 0:
+                raise RuntimeError(L.error_string(rc))
+            sec = e0.elapsed_time(e1) / 1e3
+            st = d_s.cpu().numpy().view(L.STATS_DTYPE)
+            outs[name] = (d_u.cpu().numpy(), d_h.cpu().numpy(), d_c.cpu().numpy(),
+                          d_m.cpu().numpy().view(np.uint32), st)
+            trace = None
+            if name == "fp64":   # spectrum of the last LP of frame 0 along its interior-point run
+                mk = outs[name][3][0:1]
+                in_lp = (mk != 0).astype(np.uint8)
+                qm = code.n + code.m
+                mt = 200
+                d_x = torch.zeros((1, qm), dtype=torch.float64, device="cuda")
+                d_s1 = torch.zeros(L.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+                d_t = torch.full((mt * 10,), float("nan"), dtype=torch.float64, device="cuda")
+                rc = L.lpdec_lp_solve_trace_device(d.ctx, d.code, 1, d_g[0:1],
+                                                   torch.from_numpy(in_lp).cuda(),
+                                                   torch.from_numpy(mk).cuda(), d_x, d_s1, d_t, mt)
+                torch.cuda.synchronize()
+                tr = d_t.cpu().numpy().reshape(mt, 10)
+                k = int(d_s1.cpu().numpy().view(L.STATS_DTYPE)["ipm_iters_total"][0])
+                trace = [{"it": i, "gap": float(tr[i, 0]), "pcg_iters": int(tr[i, 3]),
+                          "cond_MinvQ_lanczos": float(tr[i, 9] / tr[i, 8]) if tr[i, 8] > 0 else None}
+                         for i in range(min(k, mt)) if np.isfinite(tr[i, 0])]
+            modes[name] = {
+                "seconds": sec, "frames_per_s": nf / sec,
+                "frames_ok": int((st["status"] == 0).sum()),
+                "frames_integral": int((outs[name][2] == 1).sum()),
+                "mean_lps": float(st["alp_iters"].mean()),
+                "mean_ipm_iters": float(st["ipm_iters_total"].mean()),
+                "pcg_iters_per_ipm_iter": float(st["pcg_iters_total"].sum() /
+                                                max(1, st["ipm_iters_total"].sum())),
+                "fp64_share_of_pcg_iters": float(st["pcg_iters_fp64"].sum() /
+                                                 max(1, st["pcg_iters_total"].sum())),
+                "dense_solves": int(st["dense_solves"].sum()),
+                "vertex_failures": int(st["vertex_failures"].sum()),
+            }
+            if trace is not None:
+                modes[name]["trace_last_lp_frame0"] = trace
+    u64, h64, c64, m64, s64 = outs["fp64"]
+    u32, h32, c32, m32, s32 = outs["mixed"]
+    agree = {
+        "hard_equal": int(sum(np.array_equal(h64[f], h32[f]) for f in range(nf))),
+        "cert_equal": int((c64 == c32).sum()), "cutset_equal": int(sum(np.array_equal(m64[f], m32[f]) for f in range(nf))),
+        "max_abs_du": float(np.abs(u64 - u32).max()),
+        "max_rel_dobj": float(np.max(np.abs(s64["objective"] - s32["objective"]) /
+                                     (1 + np.abs(s64["objective"])))),
+    }
+    full = None
+    if cfut is not None:
+        res = cfut.get()
+        pool.close()
+        full = [{"frame": f, "full_lp_objective": obj,
+                 "fp64_rel_err": abs(float(s64["objective"][f]) - obj) / (1 + abs(obj)),
+                 "mixed_rel_err": abs(float(s32["objective"][f]) - obj) / (1 + abs(obj))}
+                for f, obj in res]
+    line = {
+        "metric": "c3 precision study: (3,6) n=16000 LP decoding, FP32 PCG + FP64 refinement vs FP64",
+        "value": modes["fp64"]["frames_per_s"], "unit": UNIT, "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": f"(3,6) Gallager n=16000 m=8000 (seed 0), Eb/N0 1.8 dB, frames 0..{nf - 1} "
+                               f"of the seed-0 pool (a subset of the configuration's 2000)"},
+        "modes": modes, "fp64_vs_mixed": agree, "vs_full_lp": full,
+        "full_lp": "Feldman's LP over all 8000 x 32 parity inequalities, HiGHS dual simplex on the "
+                   "host (Theorem 2(c): the LP decoding optimum)",
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the CPU oracle on the host cores
 # ---------------------------------------------------------------------------
 
@@ -580,6 +704,8 @@ def main():
         run_reference(args)
     elif args.workload in SERVING:
         run_serving(args)
+    elif args.workload == "c3":
+        run_c3(args)
     else:
         run_ours(args)
 

@@ -176,16 +176,22 @@ def msolve(A, d2, col, row, r):
     return z
 
 
-def pcg(A, d2, w, col, row, tol, max_iter, x0=None, residuals=None):
-    """Algorithm 4 on Q = A D^2 A' with the MTS preconditioner (col, row).
-    Stops when ||r||_2 / ||w||_2 < tol (r the recurrence residual)."""
+def pcg(A, d2, w, col, row, tol, max_iter, x0=None, residuals=None, coefficients=None):
+    """Algorithm 4 on Q = A D^2 A' with the MTS preconditioner (col, row);
+    col = None runs plain CG (M = I). Stops when ||r||_2 / ||w||_2 < tol (r
+    the recurrence residual). ``coefficients`` (a list) receives (alpha,
+    nu) per iteration."""
     Q = lambda v: A @ (d2 * (A.T @ v))  # noqa: E731
+    if col is None:
+        msolve_ = lambda r: r.copy()  # noqa: E731
+    else:
+        msolve_ = lambda r: msolve(A, d2, col, row, r)  # noqa: E731
     x = np.zeros_like(w) if x0 is None else x0.copy()
     r = w - Q(x)
     wn = float(np.linalg.norm(w))
     if wn == 0.0:
         return x, 0
-    z = msolve(A, d2, col, row, r)
+    z = msolve_(r)
     h = z.copy()
     zr = float(np.dot(z, r))
     it = 0
@@ -199,9 +205,11 @@ def pcg(A, d2, w, col, row, tol, max_iter, x0=None, residuals=None):
         alpha = zr / float(np.dot(h, l))
         x = x + alpha * h
         r = r - alpha * l
-        z = msolve(A, d2, col, row, r)
+        z = msolve_(r)
         zr_new = float(np.dot(z, r))
         nu = zr_new / zr
+        if coefficients is not None:
+            coefficients.append((alpha, nu))
         h = z + nu * h
         zr = zr_new
     return x, it
