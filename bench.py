@@ -71,6 +71,10 @@ def parse_args():
     ap.add_argument("--threads", type=int, default=128)
     ap.add_argument("--precond", choices=["column", "incremental", "rowwise", "adaptive"],
                     default="column", help="triangular-set preconditioner (Section V)")
+    ap.add_argument("--warm-start", type=int, default=0,
+                    help="1: interior-point warm start across the LPs of a frame")
+    ap.add_argument("--mts-reuse", type=int, default=0,
+                    help="1: reuse the triangular set across interior-point iterations")
     ap.add_argument("--smem-budget", type=int, default=0,
                     help="shared-memory bytes per CTA (0 = library choice)")
     ap.add_argument("--ebn0", type=float, default=EBN0_DB,
@@ -83,10 +87,12 @@ def parse_args():
                     help="seconds of the plain one-frame-per-launch arm (0 = skip)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per k_decode launch from an ncu capture of this build")
-    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5", "x123"], default="c2",
                     help="c2: the batched decode of the metric (default); c3: the n=16000 "
                          "precision study; c4 / c5: serving with Poisson arrivals of mixed-length "
-                         "frames (each prints one JSON line of its own)")
+                         "frames; x123: the iteration-count studies of Section III-D (each prints "
+                         "one JSON line of its own)")
+    ap.add_argument("--x-trials", type=int, default=1000, help="frames per length (x123)")
     ap.add_argument("--c3-frames", type=int, default=32,
                     help="frames of the n=16000 study (a subset of its 2000)")
     ap.add_argument("--c3-oracle-frames", type=int, default=2,
@@ -106,6 +112,7 @@ def workload_config(args, n, m):
         "frames_per_step": args.frames, "warmup_frames_per_step": args.warmup_frames,
         "precision": args.precision, "smem_budget": args.smem_budget or "library (1/3 of SM)",
         "threads_per_block": args.threads, "variant": "MALP-A", "precond": args.precond,
+        "warm_start": args.warm_start, "mts_reuse": args.mts_reuse,
         "l2": "flushed by a 256 MB write between timed steps",
     }
 
@@ -244,6 +251,8 @@ def run_ours(args):
     prm.smem_budget = args.smem_budget
     prm.precond = {"column": L.LPDEC_MTS_COLUMN, "incremental": L.LPDEC_MTS_INCREMENTAL,
                    "rowwise": L.LPDEC_MTS_ROWWISE, "adaptive": L.LPDEC_MTS_ADAPTIVE}[args.precond]
+    prm.warm_start = args.warm_start
+    prm.mts_reuse = args.mts_reuse
     dec = L.Decoder(code, device=local, params=prm)
 
     nsteps = args.warmup + args.steps
@@ -667,6 +676,63 @@ def run_c3(args):
 
 
 # ---------------------------------------------------------------------------
+# x123: iteration counts of ALP, MALP-A and MALP-B against code length
+# ---------------------------------------------------------------------------
+
+X_LENGTHS = (120, 240, 480, 720, 960, 1200, 1800, 2400)
+
+
+def run_x123(args):
+    import numpy as np
+    import torch
+    from paper_0902_0657_gb300 import build as B
+    from paper_0902_0657_gb300 import lpdec as L
+    from synth import awgn_llr_frames, named_code
+    B.build()
+    torch.cuda.set_device(0)
+    variants = (("ALP", L.LPDEC_ALP), ("MALP-A", L.LPDEC_MALP_A), ("MALP-B", L.LPDEC_MALP_B))
+    table = []
+    for n in X_LENGTHS:
+        code = named_code(f"gallager_{n}")
+        G = awgn_llr_frames(code.n, code.design_rate, 2.0, SEED, range(args.x_trials))
+        row = {"n": n}
+        largest = {}
+        for name, var in variants:
+            prm = L.lpdec_default_params()
+            prm.variant = var
+            with L.Decoder(code, params=prm) as d:
+                u, hard, cert, masks, st = d.decode_batch(G)
+            lps = st["alp_iters"].astype(float)
+            integ = cert == 1
+            ent = {}
+            for lab, sel in (("integral", integ), ("fractional", ~integ)):
+                if sel.any():
+                    ent[lab] = {"frames": int(sel.sum()), "mean_lps": float(lps[sel].mean()),
+                                "p95_lps": float(np.sort(lps[sel])[int(np.ceil(0.95 * sel.sum())) - 1]),
+                                "mean_largest_lp_rows": float(st["lp_rows_max"][sel].mean())}
+            ent["frames_ok"] = int((st["status"] == 0).sum())
+            ent["frames_switched_to_alp"] = int((st["alp_switch"] > 0).sum())
+            row[name] = ent
+            largest[name] = st["lp_rows_max"].astype(float), integ
+        for name in ("MALP-A", "MALP-B"):
+            red = {}
+            for lab, val in (("integral", True), ("fractional", False)):
+                rm, integ = largest[name]
+                ra, _ = largest["ALP"]
+                sel = (integ == val) & (ra > 0)
+                if sel.any():
+                    red[lab] = float(1.0 - rm[sel].mean() / ra[sel].mean())
+            row[f"{name}_largest_lp_reduction_vs_ALP"] = red
+        table.append(row)
+    line = {"metric": "Section III-D iteration counts (X1-X3): LPs per frame of ALP, MALP-A, MALP-B",
+            "unit": "LPs per frame", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"(3,6) Gallager codes n in {list(X_LENGTHS)} (seed 0), "
+                                   f"Eb/N0 2 dB, {args.x_trials} frames each (seed-0 pool)"},
+            "table": table}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # Reference arm: the CPU oracle on the host cores
 # ---------------------------------------------------------------------------
 
@@ -706,6 +772,8 @@ def main():
         run_serving(args)
     elif args.workload == "c3":
         run_c3(args)
+    elif args.workload == "x123":
+        run_x123(args)
     else:
         run_ours(args)
 

@@ -120,7 +120,10 @@ extern "C" {
  *                     A D^2 A' (LPs of up to 2048 rows), and so are the
  *                     remaining Newton solves of that LP
  *   variant = LPDEC_MALP_A, precision = LPDEC_FP64
- *   precond = LPDEC_MTS_COLUMN, precond_switch = 150
+ *   precond = LPDEC_MTS_COLUMN, precond_switch = 150, warm_start = 0,
+ *   mts_reuse = 0 (the paper's future work, Sections V and VII: the
+ *   previous iterate and triangular set reused; results are the same
+ *   certified vertices either way)
  *   lp_rows_cap = 0   rows one frame's LP may hold (0 = 2m). The main
  *                     workspace holds min(m, lp_rows_cap) rows, enough for
  *                     MALP (one inequality per check); a frame whose cut list
@@ -151,7 +154,16 @@ typedef struct lpdec_params {
     int32_t precond;            /* LPDEC_MTS_* */
     int32_t precond_switch;     /* PCG iterations of one Newton solve after which
                                    LPDEC_MTS_ADAPTIVE switches the LP to Algorithm 6 */
-    int32_t reserved;
+    int32_t warm_start;         /* 1: each LP of a MALP frame after the first starts the
+                                   interior-point method from the previous LP's final
+                                   iterate (x, z floored at 0.01; rows kept from the
+                                   previous LP keep their slack and dual, new rows start
+                                   cold); 0: cold start (R4) */
+    int32_t mts_reuse;          /* 1: an interior-point iteration keeps the previous
+                                   triangular set while the last PCG took <= 20
+                                   iterations and the partition x_i > z_i kept its size
+                                   (the values of M are always current) */
+    int32_t reserved[2];
 } lpdec_params;
 
 /* Per-frame results besides u / hard / cert. */
@@ -166,6 +178,8 @@ typedef struct lpdec_stats {
     int32_t pcg_iters_fp64;   /* PCG iterations run in FP64 (all of them in LPDEC_FP64) */
     int32_t dense_solves;     /* Newton systems solved by the dense Cholesky fallback */
     int32_t alp_switch;       /* LPs solved before a MALP frame continued as ALP (0: never) */
+    int32_t lp_rows_max;      /* rows of the largest LP solved */
+    int32_t reserved;
     double  objective;        /* gamma'u */
     double  pcg_flops;        /* algorithmic floating-point operations of the Newton
                                  solves: PCG iterations (Q h, both triangular

@@ -366,6 +366,7 @@ DevParams to_dev(const lpdec_params& p) {
     d.max_alp = p.max_alp; d.max_ipm = p.max_ipm; d.max_pcg = p.max_pcg;
     d.variant = p.variant; d.precision = p.precision;
     d.precond = p.precond; d.precond_switch = p.precond_switch;
+    d.warm_start = p.warm_start; d.mts_reuse = p.mts_reuse;
     return d;
 }
 
@@ -472,6 +473,8 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
         {G_QD, dense_rows > 0 ? D * (size_t)dense_rows * dense_rows : 16, 2},
         {G_CCHK2, H * P, 2}, {G_CMASK2, I * P, 2}, {G_CRPTR2, I * ((size_t)m + 1), 2},
         {G_GAM, D * (size_t)n, 2}, {G_LZ, D * (2 * (size_t)kLz + 2), 2},
+        {G_XW, D * q, 2}, {G_ZW, D * q, 2}, {G_YW, D * P, 2}, {G_PROW, I * (size_t)m, 2},
+        {G_PMASK, I * (size_t)m, 2},
     };
     Layout L{};
     size_t s = 0, g = 0;
@@ -768,6 +771,8 @@ void lpdec_default_params(lpdec_params* p) {
     p->lp_rows_cap = 0;
     p->precond = LPDEC_MTS_COLUMN;
     p->precond_switch = 150;
+    p->warm_start = 0;
+    p->mts_reuse = 0;
 }
 
 const char* lpdec_error_string(int32_t code) {

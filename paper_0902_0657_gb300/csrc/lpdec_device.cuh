@@ -47,6 +47,7 @@ struct DevParams {
     double pcg_gap_factor, tol_inner, tol_feas_loose, tol_cert, tau_inc;
     int max_alp, max_ipm, max_pcg, variant, precision;
     int precond, precond_switch;
+    int warm_start, mts_reuse;
 };
 
 // ---------------------------------------------------------------------------
@@ -83,6 +84,9 @@ enum Arr {
     G_GAM,
     // CG coefficients of the first PCG round of a traced Newton solve
     G_LZ,
+    // warm start: the previous LP's final iterate (x, z over its columns, y
+    // over its rows) and, per check, its row there and that row's set V
+    G_XW, G_ZW, G_YW, G_PROW, G_PMASK,
     A_COUNT
 };
 
@@ -116,7 +120,7 @@ struct Layout {
 __host__ __device__ constexpr bool row_sized(int a) {
     return !(a == S_FLAGS || a == S_MASK || a == S_FLIP || a == S_HPTR || a == S_VPTR ||
              a == S_CPTR || a == S_CRPTR || a == G_U || a == G_T64 || a == G_QD ||
-             a == G_CRPTR2 || a == G_GAM || a == G_LZ);
+             a == G_CRPTR2 || a == G_GAM || a == G_LZ || a == G_PROW || a == G_PMASK);
 }
 
 template <typename T>
@@ -138,6 +142,9 @@ struct WS {
     double* qd;   // dense Cholesky factor (column-major p x p), null when off
     double* gam;  // private copy of the frame's LLRs (serving)
     double* lz;   // CG coefficient record of traced solves (null when not tracing)
+    double *xw, *zw, *yw;   // warm start: previous LP's final iterate
+    int* prow;              // ... per check: its row in the previous LP (-1: none)
+    uint32_t* pmask;        // ... and that row's set V
     uint16_t* cchk2;
     uint32_t *cmask2, *crptr2;
     int cap_n, cap_p;   // capacities the sub-arrays were sliced with
@@ -192,6 +199,8 @@ __device__ inline void point_ws(WS<T>& w, const Layout& L, char* smem, char* gws
     P_(uint32_t, crptr2, G_CRPTR2);
     P_(double, gam, G_GAM);
     P_(double, lz, G_LZ);
+    P_(double, xw, G_XW); P_(double, zw, G_ZW); P_(double, yw, G_YW);
+    P_(int, prow, G_PROW); P_(uint32_t, pmask, G_PMASK);
 #undef P_
     if (!only_rows) w.lz = nullptr;   // set by the traced entry point only
     if (!only_rows) {
@@ -238,6 +247,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W) {
     v.dy = W.dy; v.r64 = W.r64; v.u = W.u; v.t64 = W.t64;
     v.vx = W.vx; v.v1 = W.v1; v.v2 = W.v2; v.v3 = W.v3; v.v4 = W.v4; v.vr1 = W.vr1;
     v.vr2 = W.vr2; v.p64 = W.p64; v.qd = W.qd; v.gam = W.gam; v.lz = W.lz;
+    v.xw = W.xw; v.zw = W.zw; v.yw = W.yw; v.prow = W.prow; v.pmask = W.pmask;
     v.cchk2 = W.cchk2; v.cmask2 = W.cmask2; v.crptr2 = W.crptr2;
     return v;
 }
@@ -2032,6 +2042,8 @@ __device__ __noinline__ int certify_basis(Blk& B, const CodeView C, WS<T> W, con
 // ---------------------------------------------------------------------------
 // Doubles per interior-point iteration in a trace (lpdec_lp_solve_trace_device).
 constexpr int kTrace = 10;
+// Least x_i, z_i of a warm start (lpdec_params.warm_start).
+constexpr double kWarmFloor = 1e-2;
 
 struct IpmOut {
     int iters, pcg_iters, pcg_iters64, converged, certified, max_levels, dense;
@@ -2043,24 +2055,46 @@ struct IpmOut {
 template <typename T>
 __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Frame& F,
                                    const DevParams& P, const double* gamma, int q2,
-                                   double* trace = nullptr, int max_trace = 0) {
+                                   double* trace = nullptr, int max_trace = 0, bool warm = false) {
     const int n = C.n, p = F.p, q = F.q;
     IpmOut o{0, 0, 0, 0, 0, 0, 0, 0.0, 0.0};
-    // cold start x = e, y = 0, z = c + e
     double nc2 = 0.0;
-    for (int i = B.tid; i < q; i += B.nt) {
-        double c = cost_of(gamma, n, i);
-        W.x[i] = 1.0;
-        W.zz[i] = c + 1.0;
-        nc2 += c * c;
+    if (!warm) {
+        // cold start x = e, y = 0, z = c + e
+        for (int i = B.tid; i < q; i += B.nt) {
+            double c = cost_of(gamma, n, i);
+            W.x[i] = 1.0;
+            W.zz[i] = c + 1.0;
+            nc2 += c * c;
+        }
+        for (int r = B.tid; r < p; r += B.nt) W.y[r] = 0.0;
+    } else {
+        // warm start from the previous LP's final iterate, pushed kWarmFloor
+        // away from the boundary; a row kept from it (same check and set)
+        // keeps its slack pair and dual, a new row starts as in a cold start
+        for (int i = B.tid; i < n; i += B.nt) {
+            double c = cost_of(gamma, n, i);
+            W.x[i] = fmax(W.xw[i], kWarmFloor);
+            W.zz[i] = fmax(W.zw[i], kWarmFloor);
+            nc2 += c * c;
+        }
+        for (int r = B.tid; r < p; r += B.nt) {
+            const int j = W.cchk[r], pr = W.prow[j];
+            const bool kept = pr >= 0 && W.pmask[j] == W.cmask[r];
+            W.x[n + r] = kept ? fmax(W.xw[n + pr], kWarmFloor) : 1.0;
+            W.zz[n + r] = kept ? fmax(W.zw[n + pr], kWarmFloor) : 1.0;
+            W.y[r] = kept ? W.yw[pr] : 0.0;
+        }
     }
-    for (int r = B.tid; r < p; r += B.nt) W.y[r] = 0.0;
     F.normc = sqrt(bsum(B, nc2));   // (barrier inside)
     bool force64 = false, force_dense = false;
     int last_pcg = 0;
     // preconditioner of this LP's Newton systems (LPDEC_MTS_ADAPTIVE starts
     // column-wise and turns incremental for good after a long PCG run)
     int kind = P.precond == LPDEC_MTS_ADAPTIVE ? LPDEC_MTS_COLUMN : P.precond;
+    Levels L{0, 0};
+    bool reuse_ok = false;
+    double nbasic_prev = -1.0;
     double prev_grel = INFINITY, sig0 = -1.0, sig1 = -1.0;
     for (int it = 0;; ++it) {
         // Expensive regime (the basis certificate keeps failing and Newton
@@ -2127,7 +2161,10 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Fram
         // w = r_b + A D^2 r_c - A Z^-1 r_e (Eq. 24 right side)
         for (int r = B.tid; r < p; r += B.nt) W.w[r] += rowA<double>(C, W, r, W.rc) + W.rc[n + r];
         __syncthreads();
-        Levels L = select_mts<T>(B, C, W, F, W.d2, kind);
+        // MTS reuse (lpdec_params.mts_reuse): keep the previous iteration's
+        // triangular set while its PCG converged fast and the partition
+        // x_i > z_i kept its size; the values of M (D_M^2) are always current
+        if (!(P.mts_reuse && reuse_ok)) L = select_mts<T>(B, C, W, F, W.d2, kind);
         o.max_levels = max(o.max_levels, max(L.nb, L.nf));
         // near the optimum the selected basis may already be optimal
         if (g_rel < P.tol_cert && certify_basis<T>(B, C, W, F, L, gamma)) {
@@ -2153,6 +2190,13 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Fram
         o.flops += no.flops;
         o.bytes += no.bytes;
         last_pcg = no.dense ? 1000000 : no.iters;
+        if (P.mts_reuse) {
+            double nb_l = 0.0;
+            for (int i = B.tid; i < q; i += B.nt) nb_l += W.x[i] > W.zz[i] ? 1.0 : 0.0;
+            const double nbasic = bsum(B, nb_l);
+            reuse_ok = last_pcg <= 20 && nbasic == nbasic_prev;
+            nbasic_prev = nbasic;
+        }
         if (P.precond == LPDEC_MTS_ADAPTIVE && (no.dense || no.iters > P.precond_switch))
             kind = LPDEC_MTS_INCREMENTAL;
         if (no.relres > 1e-3 && g_rel < 1e-6) {   // no usable direction left near the optimum
@@ -2309,11 +2353,28 @@ __device__ __noinline__ int vertex_recover(Blk& B, const CodeView C, WS<T> W, co
 // (twice the iteration cap); only if that fails too is the partition's
 // vertex taken without a certificate (counted in vertex_failures). Returns
 // whether the LP ended converged or certified; io accumulates the counts.
+// Keeps the final iterate of the LP just solved (before its vertex replaces
+// x) for the warm start of the next LP: x, z over the columns, y over the
+// rows, and per check its row and set.
+template <typename T>
+__device__ inline void save_iterate(Blk& B, const CodeView& C, WS<T>& W, const Frame& F) {
+    for (int i = B.tid; i < F.q; i += B.nt) { W.xw[i] = W.x[i]; W.zw[i] = W.zz[i]; }
+    for (int j = B.tid; j < C.m; j += B.nt) W.prow[j] = -1;
+    __syncthreads();
+    for (int r = B.tid; r < F.p; r += B.nt) {
+        W.yw[r] = W.y[r];
+        W.prow[W.cchk[r]] = r;
+        W.pmask[W.cchk[r]] = W.cmask[r];
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __device__ inline bool solve_lp(Blk& B, const CodeView& C, WS<T>& W, Frame& F,
                                 const DevParams& P, const double* gamma, lpdec_stats& st,
-                                IpmOut& io) {
-    io = ipm_solve<T>(B, C, W, F, P, gamma, 0);
+                                IpmOut& io, bool warm = false, bool keep = false) {
+    io = ipm_solve<T>(B, C, W, F, P, gamma, 0, nullptr, 0, warm);
+    if (keep) save_iterate<T>(B, C, W, F);
     int ok = io.certified || certify<T>(B, C, W, F, gamma);
     DevParams Q = P;
     Q.max_ipm = 2 * P.max_ipm;
@@ -2429,7 +2490,10 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, const WS<T>& W0,
         }
         if (!built) { status = LPDEC_ERR_OUT_OF_BUDGET; break; }
         IpmOut io;
-        const bool solved = solve_lp<T>(B, C, W, F, P, gamma, st, io);
+        // warm start (lpdec_params.warm_start) for MALP frames: one row per
+        // check, so rows are matched by check and set
+        const bool ws = P.warm_start && !alp;
+        const bool solved = solve_lp<T>(B, C, W, F, P, gamma, st, io, ws && st.alp_iters > 0, ws);
         st.alp_iters++;
         st.ipm_iters_total += io.iters;
         st.pcg_iters_total += io.pcg_iters;
@@ -2440,6 +2504,7 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, const WS<T>& W0,
         st.max_levels = max(st.max_levels, io.max_levels);
         lp_finish<T>(B, C, W, F, P);
         st.lp_rows_final = F.p;
+        st.lp_rows_max = max(st.lp_rows_max, F.p);
         if (!solved) { status = LPDEC_ERR_NOT_CONVERGED; break; }
         // Theorem 2(b): with unique LP optima the MALP cost rises strictly. A
         // cost that does not rise means that hypothesis failed and MALP may

@@ -43,13 +43,15 @@ class lpdec_params(ctypes.Structure):
                [(k, ctypes.c_int32) for k in
                 ("max_alp", "max_ipm", "max_pcg", "variant", "precision",
                  "threads_per_block", "smem_budget", "lp_rows_cap", "precond",
-                 "precond_switch", "reserved")]
+                 "precond_switch", "warm_start", "mts_reuse")] + \
+               [("reserved", ctypes.c_int32 * 2)]
 
 
 class lpdec_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in
                 ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total", "lp_rows_final",
-                 "vertex_failures", "max_levels", "pcg_iters_fp64", "dense_solves", "alp_switch")] + \
+                 "vertex_failures", "max_levels", "pcg_iters_fp64", "dense_solves", "alp_switch",
+                 "lp_rows_max", "reserved")] + \
                [(k, ctypes.c_double) for k in
                 ("objective", "pcg_flops", "seconds", "pcg_bytes", "t_start", "t_end")]
 
@@ -57,7 +59,7 @@ class lpdec_stats(ctypes.Structure):
 STATS_DTYPE = np.dtype([(k, np.int32) for k in
                         ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total",
                          "lp_rows_final", "vertex_failures", "max_levels", "pcg_iters_fp64",
-                         "dense_solves", "alp_switch")] +
+                         "dense_solves", "alp_switch", "lp_rows_max", "reserved")] +
                        [(k, np.float64) for k in
                         ("objective", "pcg_flops", "seconds", "pcg_bytes", "t_start", "t_end")])
 assert STATS_DTYPE.itemsize == ctypes.sizeof(lpdec_stats)

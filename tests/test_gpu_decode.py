@@ -26,6 +26,7 @@ def compare_frame(res, u, hard, cert, masks, st, ctx=""):
     assert st["alp_iters"] == res.alp_iters, ctx
     assert st["alp_switch"] == res.alp_switch, ctx
     assert st["lp_rows_final"] == res.lp_rows_final, ctx
+    assert st["lp_rows_max"] == max([h.p for h in res.history] or [0]), ctx
     assert np.max(np.abs(u - res.u)) <= 1e-6, ctx
     assert abs(st["objective"] - res.objective) <= 1e-6 * (1 + abs(res.objective)), ctx
 
@@ -268,4 +269,24 @@ def test_malp_b_matches_oracle():
         u, hard, cert, masks, st = d.decode_batch(G)
     for f in range(100):
         res = oracle.decode(code, G[f], OracleParams(variant="malp_b"))
+        compare_frame(res, u[f], hard[f], cert[f], masks[f], st[f], f"frame {f}")
+
+
+@pytest.mark.parametrize("warm,reuse", [(1, 0), (0, 1), (1, 1)])
+def test_warm_start_and_mts_reuse_match_oracle(warm, reuse):
+    """The paper's future work (Sections V, VII): interior-point warm starts
+    across the LPs of a frame and reuse of the triangular set across
+    interior-point iterations change the path, not the certified LP
+    solutions: decisions and values equal the oracle's (cold starts, direct
+    Newton solves)."""
+    torch_cuda()
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(200))
+    prm = L.lpdec_default_params()
+    prm.warm_start = warm
+    prm.mts_reuse = reuse
+    with L.Decoder(code, params=prm) as d:
+        u, hard, cert, masks, st = d.decode_batch(G)
+    for f in range(200):
+        res = oracle.decode(code, G[f])
         compare_frame(res, u[f], hard[f], cert[f], masks[f], st[f], f"frame {f}")
