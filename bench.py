@@ -97,7 +97,9 @@ def parse_args():
                     help="frames of the n=16000 study (a subset of its 2000)")
     ap.add_argument("--c3-oracle-frames", type=int, default=2,
                     help="frames of the study checked against the full LP (HiGHS)")
-    ap.add_argument("--serve-frames", type=int, default=3000,
+    ap.add_argument("--max-pcg", type=int, default=0,
+                    help="PCG iteration cap per Newton solve (0 = library default)")
+    ap.add_argument("--serve-frames", type=int, default=600,
                     help="frames per load level of the serving workloads")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0,
                     help="HBM admission budget of the serving workloads")
@@ -526,6 +528,7 @@ def run_serving(args):
         sat_frames = serving_frames(spec, codes, N, 0)
         el, lat, st = serve_run(srv, sat_frames)
         sat = N / el
+        print(f"[serving] saturated: {N} frames in {el:.1f} s", file=sys.stderr, flush=True)
         levels["saturated"] = {"frames_per_s": sat, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                                "p99.9_ms": 1e3 * float(np.percentile(lat, 99.9)),
@@ -533,6 +536,7 @@ def run_serving(args):
         for i, load in enumerate((0.5, 0.8, 0.95)):
             fr = serving_frames(spec, codes, N, (i + 1) * N)
             el, lat, st = serve_run(srv, fr, rate=load * sat)
+            print(f"[serving] load {load}: {N} frames in {el:.1f} s", file=sys.stderr, flush=True)
             levels[f"poisson_{int(load * 100)}pct"] = {
                 "offered_frames_per_s": load * sat, "frames_per_s": N / el,
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
@@ -594,6 +598,10 @@ def run_c3(args):
     for name, prec in (("fp64", L.LPDEC_FP64), ("mixed", L.LPDEC_MIXED)):
         prm = L.lpdec_default_params()
         prm.precision = prec
+        if args.max_pcg > 0:
+            prm.max_pcg = args.max_pcg
+        prm.precond = {"column": L.LPDEC_MTS_COLUMN, "incremental": L.LPDEC_MTS_INCREMENTAL,
+                       "rowwise": L.LPDEC_MTS_ROWWISE, "adaptive": L.LPDEC_MTS_ADAPTIVE}[args.precond]
         with L.Decoder(code, params=prm) as d:
             d_g = torch.from_numpy(G).cuda()
             d_u = torch.empty((nf, code.n), dtype=torch.float64, device="cuda")
@@ -667,7 +675,8 @@ def run_c3(args):
         "value": modes["fp64"]["frames_per_s"], "unit": UNIT, "n_gpus": 1,
         "higher_is_better": True, "data": "synthetic",
         "config": {"workload": f"(3,6) Gallager n=16000 m=8000 (seed 0), Eb/N0 1.8 dB, frames 0..{nf - 1} "
-                               f"of the seed-0 pool (a subset of the configuration's 2000)"},
+                               f"of the seed-0 pool (a subset of the configuration's 2000)",
+                   "max_pcg": args.max_pcg or 1000, "precond": args.precond},
         "modes": modes, "fp64_vs_mixed": agree, "vs_full_lp": full,
         "full_lp": "Feldman's LP over all 8000 x 32 parity inequalities, HiGHS dual simplex on the "
                    "host (Theorem 2(c): the LP decoding optimum)",

@@ -454,8 +454,9 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
         // solves), then the sparse passes of Q h, then what runs once per
         // interior-point iteration (MTS selection, level build), then the
         // cut search and the cut list
-        {S_VEC, vec, 0}, {S_BDEP, H * ea, 0}, {S_FDEP, H * ea, 0}, {S_BPTR, I * (P + 1), 0},
-        {S_FPTR, I * (P + 1), 0}, {S_LBROWS, H * P, 0}, {S_LFROWS, H * P, 0},
+        {S_VEC, vec, 0}, {S_BDEP, H * ea, 0}, {S_FDEP, H * ea, 0}, {S_LBSE, 8 * P, 0},
+        {S_LFSE, 8 * P, 0}, {S_LBROWS, H * P, 0}, {S_LFROWS, H * P, 0},
+        {S_BPTR, I * (P + 1), 0}, {S_FPTR, I * (P + 1), 0},
         {S_PSGN, P, 0}, {S_ROWENT, H * ea, 0}, {S_RPTR, I * (P + 1), 0},
         {S_COLENT, H * ea, 0}, {S_CPTR, I * ((size_t)n + 1), 0},
         {S_PIVROW, H * q, 0}, {S_PIVCOL, H * P, 0}, {S_LB, H * P, 0},

@@ -63,6 +63,7 @@ enum Arr {
     S_LB, S_LF, S_LBPTR, S_LFPTR, S_CUR, S_LBROWS, S_LFROWS, S_SELROW,
     S_DEG, S_BITMAP, S_FLAGS, S_MASK, S_FLIP, S_HPTR, S_VPTR,
     S_BPTR, S_BDEP, S_FPTR, S_FDEP,   // dependency lists of the two triangular solves
+    S_LBSE, S_LFSE,   // per level position: the dependency range of its row (sweep order)
     S_VEC,      // PCG vectors of type T: xs, r, z, h, l (pmax each), t (n), d2t (n+pmax),
                 // invd2p (pmax); during the MTS selection the same bytes hold the sort keys
                 // (u64 [q2], u32 [q2]) followed by rank [q] and sorted [q] (uint16)
@@ -132,6 +133,7 @@ struct WS {
     int *hptr, *vptr;   // shared copies of the code's CSR / CSC row pointers
     uint32_t *bptr, *fptr;
     uint16_t *bdep, *fdep;   // packed (row | kNeg): rows whose solved values row r needs
+    uint2 *lbse, *lfse;      // dependency range (begin, end) of the row at each level position
     uint8_t *cact, *psgn, *flags, *basic;
     T *xs, *r, *z, *h, *l, *t, *d2t, *invd2p;
     float *rf, *zf, *ip32;      // FP32 M-solve vectors (LPDEC_M32 only)
@@ -179,6 +181,7 @@ __device__ inline void point_ws(WS<T>& w, const Layout& L, char* smem, char* gws
     P_(int, hptr, S_HPTR); P_(int, vptr, S_VPTR);
     P_(uint32_t, bptr, S_BPTR); P_(uint32_t, fptr, S_FPTR);
     P_(uint16_t, bdep, S_BDEP); P_(uint16_t, fdep, S_FDEP);
+    P_(uint2, lbse, S_LBSE); P_(uint2, lfse, S_LFSE);
     T* v = reinterpret_cast<T*>(ws_ptr(L, S_VEC, smem, gws));
     w.skey = reinterpret_cast<unsigned long long*>(v);
     w.sidx = reinterpret_cast<uint32_t*>(w.skey + L.q2);
@@ -236,6 +239,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W) {
     v.flip = W.flip; v.psgn = W.psgn; v.deg = W.deg; v.flags = W.flags; v.basic = W.basic;
     v.hptr = W.hptr; v.vptr = W.vptr;
     v.bptr = W.bptr; v.fptr = W.fptr; v.bdep = W.bdep; v.fdep = W.fdep;
+    v.lbse = W.lbse; v.lfse = W.lfse;
     double* q = W.p64;
     v.xs = q; q += pm; v.r = q; q += pm; v.z = q; q += pm; v.h = q; q += pm; v.l = q; q += pm;
     v.t = q; q += n; v.invd2p = q;
@@ -718,6 +722,12 @@ __device__ inline Levels finish_levels(Blk& B, const CodeView& C, WS<T>& W, cons
     __syncthreads();
     for (int r = B.tid; r < p; r += B.nt) W.lfrows[atomicAdd(&W.cur[W.lf[r]], 1u)] = (uint16_t)r;
     __syncthreads();
+    for (int k = B.tid; k < p; k += B.nt) {
+        const int rb = W.lbrows[k], rf = W.lfrows[k];
+        W.lbse[k] = make_uint2(W.bptr[rb], W.bptr[rb + 1]);
+        W.lfse[k] = make_uint2(W.fptr[rf], W.fptr[rf + 1]);
+    }
+    __syncthreads();
     return L;
 }
 
@@ -1192,18 +1202,23 @@ __device__ inline void selection_order(Blk& B, WS<T>& W, const Frame& F, int32_t
 // of the row's dependencies and the leader (g == 0) finishes the row. Back:
 // out[r] = +-(r_r - sum); forward: out[r] = +-(out[r] / d_piv - sum). All 32
 // lanes of the warp call this (r < 0 marks an idle group).
+// One row of a triangular solve, reduced by a group of G lanes (G a power
+// of two <= 32, g = lane index inside the group). The lane sums its share of
+// the row's dependencies (entries begin + g, begin + g + G, ...; the first
+// two, d0 and d1, already loaded, kNone when absent) and the group reduces;
+// the leader (g == 0) finishes the row. Back: out[r] = +-(r_r - sum);
+// forward: out[r] = +-(out[r] / d_piv - sum). All 32 lanes of the warp call
+// this (r < 0 marks an idle group).
 template <typename T, bool kBack, bool kScale = true>
-__device__ __forceinline__ void solve_row(WS<T>& W, int r, int g, int G, T* rvec, T* out,
-                                          T alpha) {
+__device__ __forceinline__ void solve_row(WS<T>& W, const uint16_t* dep, int r, uint32_t e,
+                                          uint32_t k2, uint16_t d0, uint16_t d1, int G, int g,
+                                          T* rvec, T* out, T alpha) {
     T acc = T(0);
-    if (r >= 0) {
-        const uint32_t* ptr = kBack ? W.bptr : W.fptr;
-        const uint16_t* dep = kBack ? W.bdep : W.fdep;
-        const int k1 = ptr[r + 1];
-        for (int k = ptr[r] + g; k < k1; k += G) {
-            uint16_t ent = dep[k];
-            acc += signed_val<T>(ent, out[ent & kIdx]);
-        }
+    if (d0 != kNone) acc += signed_val<T>(d0, out[d0 & kIdx]);
+    if (d1 != kNone) acc += signed_val<T>(d1, out[d1 & kIdx]);
+    for (uint32_t k = k2; k < e; k += G) {
+        const uint16_t ent = dep[k];
+        acc += signed_val<T>(ent, out[ent & kIdx]);
     }
     for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o, G);
     if (r >= 0 && g == 0) {
@@ -1223,33 +1238,81 @@ __device__ __forceinline__ void solve_row(WS<T>& W, int r, int g, int G, T* rvec
     }
 }
 
+// The row at level position idx (< end) for lane group g of size G: its
+// index, dependency range and first two dependency entries of the lane.
+struct RowSlot {
+    int r;
+    uint32_t e, k2;
+    uint16_t d0, d1;
+};
+__device__ __forceinline__ RowSlot load_slot(const uint16_t* rows, const uint2* se,
+                                             const uint16_t* dep, int idx, int end, int G, int g) {
+    RowSlot t{-1, 0u, 0u, kNone, kNone};
+    if (idx < end) {
+        t.r = rows[idx];
+        const uint2 v = se[idx];
+        const uint32_t k0 = v.x + g;
+        t.e = v.y;
+        t.d0 = k0 < v.y ? dep[k0] : kNone;
+        t.d1 = k0 + G < v.y ? dep[k0 + G] : kNone;
+        t.k2 = k0 + 2 * G;
+    }
+    return t;
+}
+
+__device__ __forceinline__ int group_of(int cnt) {
+    return cnt <= 4 ? 8 : cnt <= 8 ? 4 : cnt <= 16 ? 2 : 1;
+}
+
 // Runs rows level by level. Levels wider than two warps use every thread of
 // the CTA (one row per thread) and a CTA barrier; narrower levels (most of
 // them: the schedules are deep and thin) run on one warp (B.sw) with G lanes
-// per row and warp barriers.
+// per row and warp barriers. On that warp the next level's first rows (row,
+// dependency range, the lane's first two dependency entries: none of them
+// depends on the values being solved) are loaded before the current level's
+// barrier, so a level's dependent chain starts at the solved values.
 template <typename T, bool kBack, bool kScale = true>
 __device__ inline void level_sweep(Blk& B, WS<T>& W, const uint32_t* ptr, const uint16_t* rows,
-                                   int nlev, T* rvec, T* out, T alpha) {
+                                   const uint2* se, int nlev, T* rvec, T* out, T alpha) {
+    const uint16_t* dep = kBack ? W.bdep : W.fdep;
     bool warp_mode = false;
+    RowSlot pre{-1, 0u, 0u, kNone, kNone};
+    bool have_pre = false;   // pre holds the first pass of the level about to run
+    int i1 = nlev >= 1 ? (int)ptr[1] : 0;
     for (int lev = 1; lev <= nlev; ++lev) {
-        const int i0 = ptr[lev], i1 = ptr[lev + 1];
+        const int i0 = i1;
+        i1 = ptr[lev + 1];
         const int cnt = i1 - i0;
         if (cnt > 64 && B.nt > 32) {
             if (warp_mode) __syncthreads();
             for (int base = i0; base < i1; base += B.nt) {   // uniform trip count per warp
-                int idx = base + B.tid;
-                solve_row<T, kBack, kScale>(W, idx < i1 ? rows[idx] : -1, 0, 1, rvec, out, alpha);
+                const RowSlot t = load_slot(rows, se, dep, base + B.tid, i1, 1, 0);
+                solve_row<T, kBack, kScale>(W, dep, t.r, t.e, t.k2, t.d0, t.d1, 1, 0, rvec, out,
+                                            alpha);
             }
             __syncthreads();
             warp_mode = false;
+            have_pre = false;
         } else {
             if (B.warp == B.sw) {
-                const int G = cnt <= 4 ? 8 : cnt <= 8 ? 4 : cnt <= 16 ? 2 : 1;
-                const int per = 32 / G;
+                const int G = group_of(cnt);
+                const int per = 32 / G, g = B.lane & (G - 1);
                 for (int base = i0; base < i1; base += per) {
-                    int idx = base + B.lane / G;
-                    solve_row<T, kBack, kScale>(W, idx < i1 ? rows[idx] : -1, B.lane & (G - 1), G,
-                                                rvec, out, alpha);
+                    const RowSlot t = (base == i0 && have_pre)
+                                          ? pre
+                                          : load_slot(rows, se, dep, base + B.lane / G, i1, G, g);
+                    solve_row<T, kBack, kScale>(W, dep, t.r, t.e, t.k2, t.d0, t.d1, G, g, rvec,
+                                                out, alpha);
+                }
+                // next level's first pass, if it runs on this warp
+                have_pre = false;
+                if (lev < nlev) {
+                    const int n1 = ptr[lev + 2], c1 = n1 - i1;
+                    if (!(c1 > 64 && B.nt > 32)) {
+                        const int G1 = group_of(c1);
+                        pre = load_slot(rows, se, dep, i1 + B.lane / G1, n1, G1, B.lane & (G1 - 1));
+                        have_pre = true;
+                    }
                 }
                 __syncwarp();
             }
@@ -1324,8 +1387,8 @@ __device__ inline void level_sweep32(Blk& B, WS<T>& W, const uint32_t* ptr, cons
 template <typename T>
 __device__ inline void msolve(Blk& B, const CodeView& C, WS<T>& W, const Levels& L,
                               T* rvec, T* out, T alpha) {
-    level_sweep<T, true>(B, W, W.lbptr, W.lbrows, L.nb, rvec, out, alpha);
-    level_sweep<T, false>(B, W, W.lfptr, W.lfrows, L.nf, rvec, out, alpha);
+    level_sweep<T, true>(B, W, W.lbptr, W.lbrows, W.lbse, L.nb, rvec, out, alpha);
+    level_sweep<T, false>(B, W, W.lfptr, W.lfrows, W.lfse, L.nf, rvec, out, alpha);
 }
 
 // M-solve in FP32: zf = M^-1 rf (rf written by the caller before a barrier).
@@ -1874,7 +1937,7 @@ __device__ __noinline__ int certify(Blk& B, const CodeView C, WS<T> W, const Fra
     }
     double2 nb = bsum2(B, nbasic, 0.0);
     cmax = -bmin2(B, -cmax, 0.0).x;
-    const int max_it = min(2 * (int)nb.x + 50, 1000);
+    const int max_it = 2 * (int)nb.x + 50;   // CG on the basis: at most its size in exact arithmetic
     // --- primal: CGLS on A_B d = s, s = b - A_B x_B
     double* d = W.v1; double* g = W.v2; double* h = W.v3; double* sr = W.vr1; double* lr = W.vr2;
     double ss = 0.0, bb = 0.0;
@@ -2000,7 +2063,7 @@ __device__ __noinline__ int certify_basis(Blk& B, const CodeView C, WS<T> W, con
     for (int r = B.tid; r < p; r += B.nt) rhs[r] = W.b[r];
     for (int i = B.tid; i < q; i += B.nt) cmax = fmax(cmax, cost_of(gamma, n, i));
     __syncthreads();
-    level_sweep<double, true>(B, D, W.lbptr, W.lbrows, L.nb, rhs, out, 0.0);
+    level_sweep<double, true>(B, D, W.lbptr, W.lbrows, W.lbse, L.nb, rhs, out, 0.0);
     // x^ over the columns (pivot column of row r gets out[r])
     double mnx = INFINITY;
     for (int i = B.tid; i < q; i += B.nt) W.vx[i] = 0.0;
@@ -2022,7 +2085,7 @@ __device__ __noinline__ int certify_basis(Blk& B, const CodeView C, WS<T> W, con
     cmax = -m0.y;
     const double tol = 1e-11 * (1.0 + cmax);
     if (!(m0.x >= -tol)) return 0;
-    level_sweep<double, false, false>(B, D, W.lfptr, W.lfrows, L.nf, rhs, out, 0.0);
+    level_sweep<double, false, false>(B, D, W.lfptr, W.lfrows, W.lfse, L.nf, rhs, out, 0.0);
     double zmin = INFINITY, comp = 0.0;
     for (int i = B.tid; i < q; i += B.nt) {
         double aty = (i < n) ? colA_T<double>(C, W, i, out) : out[i - n];
