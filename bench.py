@@ -75,6 +75,9 @@ def parse_args():
                     help="1: interior-point warm start across the LPs of a frame")
     ap.add_argument("--mts-reuse", type=int, default=0,
                     help="1: reuse the triangular set across interior-point iterations")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: pick the triangular-solve schedule with lpdec_autotune during the "
+                         "warm-up (456 frames of the same code at 3 dB)")
     ap.add_argument("--smem-budget", type=int, default=0,
                     help="shared-memory bytes per CTA (0 = library choice)")
     ap.add_argument("--ebn0", type=float, default=EBN0_DB,
@@ -257,6 +260,16 @@ def run_ours(args):
     prm.mts_reuse = args.mts_reuse
     dec = L.Decoder(code, device=local, params=prm)
 
+    tune = None
+    if args.autotune:   # part of the warm-up: the schedule autotuner on a fast sample
+        sample = awgn_llr_frames(n, code.design_rate, 3.0, SEED + 1, range(456))
+        rc, pol, secs = L.lpdec_autotune(dec.ctx, dec.code, sample)
+        if rc != 0:
+            raise RuntimeError(f"autotune failed: {L.error_string(rc)}")
+        tune = {"lane_policy": pol, "candidates": dict(zip(["0", "1", "2", "4", "8"],
+                                                           [round(float(x), 3) for x in secs])),
+                "sample": "456 frames of the code at 3 dB (seed 1), total CTA seconds"}
+
     nsteps = args.warmup + args.steps
     sizes = [min(args.warmup_frames, B_) if k < args.warmup else B_ for k in range(nsteps)]
     gam = [torch.from_numpy(awgn_llr_frames(n, code.design_rate, args.ebn0, SEED,
@@ -394,7 +407,7 @@ def run_ours(args):
         "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic", "config": workload_config(args, n, m),
         "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
-        "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
+        "roofline": roofline, "cpu_baseline": cpu, "plain": plain, "schedule": tune,
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
                        "p99": 1e3 * float(np.percentile(lat, 99)),
                        "p99.9": 1e3 * float(np.percentile(lat, 99.9)),

@@ -163,7 +163,11 @@ typedef struct lpdec_params {
                                    triangular set while the last PCG took <= 20
                                    iterations and the partition x_i > z_i kept its size
                                    (the values of M are always current) */
-    int32_t reserved[2];
+    int32_t lane_policy;        /* lanes per row in the single-warp levels of the
+                                   triangular solves: 0 = by the level's width (8 lanes
+                                   for up to 4 rows, 4 up to 8, 2 up to 16, else 1), or a
+                                   fixed 1, 2, 4 or 8 (see lpdec_autotune) */
+    int32_t reserved;
 } lpdec_params;
 
 /* Per-frame results besides u / hard / cert. */
@@ -292,6 +296,17 @@ int32_t lpdec_decode_mixed_device(lpdec_ctx* ctx, int32_t nframes, const lpdec_c
                                   const double* d_gamma, double* d_u, uint8_t* d_hard,
                                   int32_t* d_cert, uint32_t* d_cut_mask, lpdec_stats* d_stats,
                                   void* stream);
+
+/* Schedule autotuner (no counterpart in the paper): decodes the host
+ * sample gamma[nframes x n] once per candidate lanes-per-row schedule of the
+ * triangular solves (lane_policy 0, 1, 2, 4, 8), keeps in the context the
+ * one with the least total device time of the frames on their CTAs, and
+ * writes it to *policy_out (optional); seconds_out[5] (optional) receives
+ * each candidate's total. A schedule changes only the order in which a
+ * row's dependency sum is added (rounding); the decoded results are the
+ * same certified LP vertices. */
+int32_t lpdec_autotune(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                       const double* gamma, int32_t* policy_out, double* seconds_out);
 
 /* ---- Single steps of the hot path (device pointers, asynchronous) ----
  * These run the same device code as the decoder on caller-given state, one

@@ -62,7 +62,8 @@ __device__ __forceinline__ int next_frame(Blk& B, int* counter, int* slot) {
     if (threadIdx.x == 0) ks.sw = serial_warp(B.nwarps);                        \
     __syncthreads();                                                            \
     B.sw = ks.sw;                                                               \
-    WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.stride);
+    WS<T> W = make_ws<T>(L, smem, gscratch + (size_t)blockIdx.x * L.stride);            \
+    W.lanes = P.lane_policy;
 
 // Where frame f of a batch lives: its code (index into the batch's code
 // table) and the offsets of its bits and checks in the packed (ragged)
@@ -367,6 +368,7 @@ DevParams to_dev(const lpdec_params& p) {
     d.variant = p.variant; d.precision = p.precision;
     d.precond = p.precond; d.precond_switch = p.precond_switch;
     d.warm_start = p.warm_start; d.mts_reuse = p.mts_reuse;
+    d.lane_policy = p.lane_policy;
     return d;
 }
 
@@ -648,6 +650,9 @@ bool params_ok(const lpdec_params& p) {
     if (p.precision != LPDEC_FP64 && p.precision != LPDEC_MIXED && p.precision != LPDEC_M32)
         return false;
     if (p.precond < LPDEC_MTS_COLUMN || p.precond > LPDEC_MTS_ADAPTIVE) return false;
+    if (p.lane_policy != 0 && p.lane_policy != 1 && p.lane_policy != 2 && p.lane_policy != 4 &&
+        p.lane_policy != 8)
+        return false;
     return p.lp_rows_cap >= 0;
 }
 
@@ -774,6 +779,7 @@ void lpdec_default_params(lpdec_params* p) {
     p->precond_switch = 150;
     p->warm_start = 0;
     p->mts_reuse = 0;
+    p->lane_policy = 0;
 }
 
 const char* lpdec_error_string(int32_t code) {
@@ -1075,6 +1081,50 @@ int32_t lpdec_decode_mixed_device(lpdec_ctx* ctx, int32_t nframes, const lpdec_c
     std::lock_guard<std::mutex> g(ctx->mu);
     return launch_decode_mixed(ctx, nframes, codes, d_gamma, d_u, d_hard, d_cert, d_cut_mask,
                                d_stats, (cudaStream_t)stream);
+}
+
+// Picks the warp-mode sweep schedule (lanes per row) for this context and
+// code: decodes the sample once per candidate and keeps the one with the
+// least total device time of the frames on their CTAs (the sum of
+// stats.seconds, which a launch's slowest frame does not dominate).
+int32_t lpdec_autotune(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                       const double* gamma, int32_t* policy_out, double* seconds_out) {
+    int32_t rc = check_ctx_code(ctx, code);
+    if (rc) return rc;
+    if (nframes < 1 || !gamma) return LPDEC_ERR_INVALID_ARG;
+    for (size_t k = 0; k < (size_t)nframes * code->n; ++k)
+        if (!std::isfinite(gamma[k])) return LPDEC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    const size_t nf = (size_t)nframes, n = code->n;
+    const size_t o_g = 0, o_u = align_up(nf * n * 8, 256), o_h = align_up(o_u + nf * n * 8, 256);
+    const size_t o_c = align_up(o_h + nf * n, 256), o_s = align_up(o_c + nf * 4, 256);
+    const size_t tot = align_up(o_s + nf * sizeof(lpdec_stats), 256);
+    rc = staging(ctx, tot);
+    if (rc) return rc;
+    char* b = ctx->staging;
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(b + o_g, gamma, nf * n * 8, cudaMemcpyHostToDevice, s));
+    std::vector<lpdec_stats> st(nf);
+    const int cand[5] = {0, 1, 2, 4, 8};
+    const int keep = ctx->prm.lane_policy;
+    int best = keep;
+    double best_t = INFINITY;
+    for (int k = 0; k < 5; ++k) {
+        ctx->prm.lane_policy = cand[k];
+        rc = launch_decode(ctx, code, nframes, (const double*)(b + o_g), (double*)(b + o_u),
+                           (uint8_t*)(b + o_h), (int32_t*)(b + o_c), nullptr,
+                           (lpdec_stats*)(b + o_s), s);
+        if (rc) { ctx->prm.lane_policy = keep; return rc; }
+        CK(cudaMemcpyAsync(st.data(), b + o_s, nf * sizeof(lpdec_stats), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double t = 0.0;
+        for (const auto& x : st) t += x.seconds;
+        if (seconds_out) seconds_out[k] = t;
+        if (t < best_t) { best_t = t; best = cand[k]; }
+    }
+    ctx->prm.lane_policy = best;
+    if (policy_out) *policy_out = best;
+    return LPDEC_OK;
 }
 
 int32_t lpdec_cut_search_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,

@@ -48,6 +48,7 @@ struct DevParams {
     int max_alp, max_ipm, max_pcg, variant, precision;
     int precond, precond_switch;
     int warm_start, mts_reuse;
+    int lane_policy;
 };
 
 // ---------------------------------------------------------------------------
@@ -150,6 +151,7 @@ struct WS {
     uint16_t* cchk2;
     uint32_t *cmask2, *crptr2;
     int cap_n, cap_p;   // capacities the sub-arrays were sliced with
+    int lanes;          // lanes per row of the warp-mode sweeps (0: by level width)
     int dense_p;        // rows the dense fallback's matrix holds (0: off)
 };
 
@@ -212,6 +214,7 @@ __device__ inline void point_ws(WS<T>& w, const Layout& L, char* smem, char* gws
     }
     w.cap_n = n;
     w.cap_p = pm;
+    if (!only_rows) w.lanes = 0;
 }
 
 template <typename T>
@@ -231,6 +234,7 @@ __device__ inline WS<double> fp64_view(const WS<T>& W) {
     v.cap_n = n;
     v.cap_p = pm;
     v.dense_p = W.dense_p;
+    v.lanes = W.lanes;
     v.rowent = W.rowent; v.colent = W.colent; v.cchk = W.cchk; v.cmask = W.cmask;
     v.cact = W.cact; v.rptr = W.rptr; v.cptr = W.cptr; v.crptr = W.crptr;
     v.pivcol = W.pivcol; v.pivrow = W.pivrow; v.lb = W.lb; v.lf = W.lf; v.lbrows = W.lbrows;
@@ -1260,7 +1264,11 @@ __device__ __forceinline__ RowSlot load_slot(const uint16_t* rows, const uint2* 
     return t;
 }
 
-__device__ __forceinline__ int group_of(int cnt) {
+// Lanes per row of a warp-mode level of cnt rows: by the level's width
+// (policy 0: 8 lanes for up to 4 rows, 4 up to 8, 2 up to 16, else 1) or a
+// fixed 1, 2, 4 or 8 (the schedule the autotuner picks, lpdec_autotune).
+__device__ __forceinline__ int group_of(int cnt, int policy) {
+    if (policy == 1 || policy == 2 || policy == 4 || policy == 8) return policy;
     return cnt <= 4 ? 8 : cnt <= 8 ? 4 : cnt <= 16 ? 2 : 1;
 }
 
@@ -1295,7 +1303,7 @@ __device__ inline void level_sweep(Blk& B, WS<T>& W, const uint32_t* ptr, const 
             have_pre = false;
         } else {
             if (B.warp == B.sw) {
-                const int G = group_of(cnt);
+                const int G = group_of(cnt, W.lanes);
                 const int per = 32 / G, g = B.lane & (G - 1);
                 for (int base = i0; base < i1; base += per) {
                     const RowSlot t = (base == i0 && have_pre)
@@ -1309,7 +1317,7 @@ __device__ inline void level_sweep(Blk& B, WS<T>& W, const uint32_t* ptr, const 
                 if (lev < nlev) {
                     const int n1 = ptr[lev + 2], c1 = n1 - i1;
                     if (!(c1 > 64 && B.nt > 32)) {
-                        const int G1 = group_of(c1);
+                        const int G1 = group_of(c1, W.lanes);
                         pre = load_slot(rows, se, dep, i1 + B.lane / G1, n1, G1, B.lane & (G1 - 1));
                         have_pre = true;
                     }

@@ -43,8 +43,7 @@ class lpdec_params(ctypes.Structure):
                [(k, ctypes.c_int32) for k in
                 ("max_alp", "max_ipm", "max_pcg", "variant", "precision",
                  "threads_per_block", "smem_budget", "lp_rows_cap", "precond",
-                 "precond_switch", "warm_start", "mts_reuse")] + \
-               [("reserved", ctypes.c_int32 * 2)]
+                 "precond_switch", "warm_start", "mts_reuse", "lane_policy", "reserved")]
 
 
 class lpdec_stats(ctypes.Structure):
@@ -104,6 +103,7 @@ def _load():
     lib.lpdec_decode_frames.argtypes = [P, P, i32, P, P, P, P, P, P]
     lib.lpdec_decode_batch.argtypes = [P, i32, P, P, P, P, P, P, P]
     lib.lpdec_decode_mixed_device.argtypes = [P, i32, P, P, P, P, P, P, P, P]
+    lib.lpdec_autotune.argtypes = [P, P, i32, P, ctypes.POINTER(i32), P]
     lib.lpdec_decode_batch_device.argtypes = [P, P, i32, P, P, P, P, P, P, P]
     lib.lpdec_cut_search_device.argtypes = [P, P, i32, P, P, P, P, P, P]
     lib.lpdec_mts_select_device.argtypes = [P, P, i32, P, P, P, P, P, P, P]
@@ -127,7 +127,7 @@ def _load():
                  "lpdec_server_stats", "lpdec_server_destroy"):
         getattr(lib, name).restype = i32
     for name in ("lpdec_ctx_create", "lpdec_ctx_set_params", "lpdec_code_create",
-                 "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_frames",
+                 "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_frames", "lpdec_autotune",
                  "lpdec_decode_mixed_device", "lpdec_decode_batch_device",
                  "lpdec_cut_search_device", "lpdec_mts_select_device", "lpdec_pcg_device",
                  "lpdec_pcg_trace_device",
@@ -274,6 +274,18 @@ def lpdec_decode_mixed_device(ctx, codes, d_gamma, d_u, d_hard, d_cert, d_cut_ma
     return _load().lpdec_decode_mixed_device(ctx, nf, ch, _dptr(d_gamma), _dptr(d_u),
                                              _dptr(d_hard), _dptr(d_cert), _dptr(d_cut_mask),
                                              _dptr(d_stats), _stream(stream))
+
+
+def lpdec_autotune(ctx, code, gamma):
+    """(status, chosen lane policy, per-candidate total device seconds for
+    policies 0, 1, 2, 4, 8) on the host sample gamma [nframes x n]."""
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    nf = gamma.shape[0]
+    pol = ctypes.c_int32()
+    secs = np.zeros(5, np.float64)
+    rc = _load().lpdec_autotune(ctx, code, nf, gamma.ctypes.data, ctypes.byref(pol),
+                                secs.ctypes.data)
+    return rc, pol.value, secs
 
 
 def lpdec_decode_batch_device(ctx, code, nframes, d_gamma, d_u, d_hard, d_cert,

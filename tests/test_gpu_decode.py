@@ -290,3 +290,27 @@ def test_warm_start_and_mts_reuse_match_oracle(warm, reuse):
     for f in range(200):
         res = oracle.decode(code, G[f])
         compare_frame(res, u[f], hard[f], cert[f], masks[f], st[f], f"frame {f}")
+
+
+def test_autotune_picks_a_schedule_and_decodes_exactly():
+    """lpdec_autotune times every lanes-per-row schedule of the triangular
+    solves on a sample and keeps the fastest in the context; decoding with
+    it (and with each fixed schedule) still gives the oracle's results."""
+    torch_cuda()
+    code = named_code("gallager_120")
+    sample = awgn_llr_frames(code.n, code.design_rate, 3.0, 1, range(64))
+    G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(60))
+    ref = [oracle.decode(code, g) for g in G]
+    with L.Decoder(code) as d:
+        rc, pol, secs = L.lpdec_autotune(d.ctx, d.code, sample)
+        assert rc == 0 and pol in (0, 1, 2, 4, 8) and np.all(secs > 0)
+        u, hard, cert, masks, st = d.decode_batch(G)
+    for f in range(60):
+        compare_frame(ref[f], u[f], hard[f], cert[f], masks[f], st[f], f"tuned {pol}, frame {f}")
+    for pol in (1, 2, 4, 8):
+        prm = L.lpdec_default_params()
+        prm.lane_policy = pol
+        with L.Decoder(code, params=prm) as d:
+            u, hard, cert, masks, st = d.decode_batch(G)
+        for f in range(60):
+            compare_frame(ref[f], u[f], hard[f], cert[f], masks[f], st[f], f"policy {pol}, frame {f}")
