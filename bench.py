@@ -75,6 +75,8 @@ def parse_args():
                     help="1: interior-point warm start across the LPs of a frame")
     ap.add_argument("--mts-reuse", type=int, default=0,
                     help="1: reuse the triangular set across interior-point iterations")
+    ap.add_argument("--order", type=int, default=1,
+                    help="frame order: 0 as given, 1 hardest first when frames queue (default), 2 always")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: pick the triangular-solve schedule with lpdec_autotune during the "
                          "warm-up (456 frames of the same code at 3 dB)")
@@ -90,8 +92,9 @@ def parse_args():
                     help="seconds of the plain one-frame-per-launch arm (0 = skip)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per k_decode launch from an ncu capture of this build")
-    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5", "x123"], default="c2",
-                    help="c2: the batched decode of the metric (default); c3: the n=16000 "
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5", "x123"], default="c2",
+                    help="c2: the batched decode of the metric (default); c1: n=120, one frame "
+                         "per launch against one batched launch; c3: the n=16000 "
                          "precision study; c4 / c5: serving with Poisson arrivals of mixed-length "
                          "frames; x123: the iteration-count studies of Section III-D (each prints "
                          "one JSON line of its own)")
@@ -117,7 +120,7 @@ def workload_config(args, n, m):
         "frames_per_step": args.frames, "warmup_frames_per_step": args.warmup_frames,
         "precision": args.precision, "smem_budget": args.smem_budget or "library (1/3 of SM)",
         "threads_per_block": args.threads, "variant": "MALP-A", "precond": args.precond,
-        "warm_start": args.warm_start, "mts_reuse": args.mts_reuse,
+        "warm_start": args.warm_start, "mts_reuse": args.mts_reuse, "order_frames": args.order,
         "l2": "flushed by a 256 MB write between timed steps",
     }
 
@@ -258,6 +261,7 @@ def run_ours(args):
                    "rowwise": L.LPDEC_MTS_ROWWISE, "adaptive": L.LPDEC_MTS_ADAPTIVE}[args.precond]
     prm.warm_start = args.warm_start
     prm.mts_reuse = args.mts_reuse
+    prm.order_frames = args.order
     dec = L.Decoder(code, device=local, params=prm)
 
     tune = None
@@ -282,6 +286,12 @@ def run_ours(args):
     d_s = torch.empty(B_ * L.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    # kernels of one timed step: the decode kernel, plus the order keys and
+    # their sort when the batch is handed out hardest-first
+    rc, grid, ordered = L.lpdec_batch_grid(dec.ctx, dec.code, B_)
+    if rc != 0:
+        raise RuntimeError(f"launch query failed: {L.error_string(rc)}")
+    launches = args.steps * (1 + 2 * ordered)
 
     def step(k):
         rc = L.lpdec_decode_batch_device(dec.ctx, dec.code, sizes[k], gam[k], d_u, d_h, d_c, d_m,
@@ -406,7 +416,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic", "config": workload_config(args, n, m),
-        "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
+        "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
         "roofline": roofline, "cpu_baseline": cpu, "plain": plain, "schedule": tune,
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
                        "p99": 1e3 * float(np.percentile(lat, 99)),
@@ -419,6 +429,7 @@ def run_ours(args):
                             "max": 1e3 * float(st["seconds"].max()),
                             "what": "device time of one frame on its CTA"},
         "detail": {
+            "grid_ctas": grid, "frames_ordered_hardest_first": bool(ordered),
             "frames_integral": float((np.concatenate(certs_all) == 1).mean()),
             "frames_ok": int((st["status"] == L.LPDEC_OK).sum()),
             "frames_not_converged": int((st["status"] == L.LPDEC_ERR_NOT_CONVERGED).sum()),
@@ -698,6 +709,63 @@ def run_c3(args):
 
 
 # ---------------------------------------------------------------------------
+# c1: the plain form (one frame per launch) against the batched form
+# ---------------------------------------------------------------------------
+
+def run_c1(args):
+    import numpy as np
+    import torch
+    from paper_0902_0657_gb300 import build as B
+    from paper_0902_0657_gb300 import lpdec as L
+    from synth import awgn_llr_frames, named_code
+    B.build()
+    torch.cuda.set_device(0)
+    code = named_code("gallager_120")
+    nf = 200
+    G = torch.from_numpy(awgn_llr_frames(code.n, code.design_rate, 2.0, SEED, range(nf))).cuda()
+    out = {}
+    with L.Decoder(code) as d:
+        d_u = torch.empty((nf, code.n), dtype=torch.float64, device="cuda")
+        d_h = torch.empty((nf, code.n), dtype=torch.uint8, device="cuda")
+        d_c = torch.empty(nf, dtype=torch.int32, device="cuda")
+        d_s = torch.empty(nf * L.STATS_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        stream = torch.cuda.current_stream()
+        for _ in range(3):   # warm-up
+            L.lpdec_decode_batch_device(d.ctx, d.code, nf, G, d_u, d_h, d_c, None, d_s, stream=stream)
+        torch.cuda.synchronize()
+        for form in ("plain", "batched"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if form == "plain":
+                for f in range(nf):
+                    rc = L.lpdec_decode_batch_device(d.ctx, d.code, 1, G[f:f + 1], d_u[f:f + 1],
+                                                     d_h[f:f + 1], d_c[f:f + 1], None,
+                                                     d_s[f * L.STATS_DTYPE.itemsize:],
+                                                     stream=stream)
+                    assert rc == 0
+            else:
+                rc = L.lpdec_decode_batch_device(d.ctx, d.code, nf, G, d_u, d_h, d_c, None, d_s,
+                                                 stream=stream)
+                assert rc == 0
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            st = d_s.cpu().numpy().view(L.STATS_DTYPE)
+            out[form] = {"frames_per_s": nf / sec, "seconds": sec,
+                         "frame_device_ms_p50": 1e3 * float(np.percentile(st["seconds"], 50)),
+                         "frame_device_ms_p99": 1e3 * float(np.percentile(st["seconds"], 99)),
+                         "frames_ok": int((st["status"] == 0).sum())}
+    line = {"metric": "c1: (3,6) n=120 LP decoding, plain form (one frame per launch) vs one batched "
+                      "launch", "value": out["batched"]["frames_per_s"], "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "(3,6) Gallager n=120 m=60 (seed 0), Eb/N0 2 dB, 200 frames "
+                                   "(seed 0), FP64, device-timed with CUDA events"},
+            "forms": out,
+            "batched_over_plain": out["batched"]["frames_per_s"] / out["plain"]["frames_per_s"]}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # x123: iteration counts of ALP, MALP-A and MALP-B against code length
 # ---------------------------------------------------------------------------
 
@@ -796,6 +864,8 @@ def main():
         run_c3(args)
     elif args.workload == "x123":
         run_x123(args)
+    elif args.workload == "c1":
+        run_c1(args)
     else:
         run_ours(args)
 

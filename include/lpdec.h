@@ -167,7 +167,12 @@ typedef struct lpdec_params {
                                    triangular solves: 0 = by the level's width (8 lanes
                                    for up to 4 rows, 4 up to 8, 2 up to 16, else 1), or a
                                    fixed 1, 2, 4 or 8 (see lpdec_autotune) */
-    int32_t reserved;
+    int32_t order_frames;       /* order in which the CTAs of a one-code batch take its
+                                   frames: 0 = as given; 1 (default) = when more frames
+                                   than CTAs, those expected to need the most LPs first
+                                   (largest sum of -gamma_i over gamma_i < 0), so the
+                                   slow ones do not start last; 2 = always. Results do
+                                   not depend on the order. */
 } lpdec_params;
 
 /* Per-frame results besides u / hard / cert. */
@@ -284,6 +289,17 @@ int32_t lpdec_decode_batch_device(lpdec_ctx* ctx, const lpdec_code* code,
                                   double* d_u, uint8_t* d_hard, int32_t* d_cert,
                                   uint32_t* d_cut_mask, lpdec_stats* d_stats,
                                   void* stream);
+
+/* Launch shape of a one-code batch under the context's parameters (host
+ * query, no allocation, no launch): *grid = the CTAs (persistent, one frame
+ * at a time each) that lpdec_decode_frames / lpdec_decode_batch_device use
+ * for nframes frames of `code` (0 for none); *ordered (may be NULL) = 1 when
+ * that batch is handed out in the hardest-first order of order_frames, which
+ * adds two small kernels (keys, sort) before the decode kernel. Returns
+ * LPDEC_ERR_INVALID_ARG for a NULL pointer, nframes < 0, a code of another
+ * device, or a code whose workspace does not fit an SM. */
+int32_t lpdec_batch_grid(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                         int32_t* grid, int32_t* ordered);
 
 /* Device form of lpdec_decode_batch, asynchronous on `stream`: codes is a
  * HOST array of nframes code handles; the device arrays are ragged and

@@ -74,6 +74,50 @@ struct FrameDesc {
     long long on, om;
 };
 
+// Frame order of a batch (lpdec_params.order_frames): frames expected to
+// need the most LPs go first, so that the slow ones do not start last and
+// leave the other CTAs idle at the end of a launch. The expectation is the
+// total reliability of the hard decision's errors, sum over gamma_i < 0 of
+// -gamma_i (correlation 0.56-0.64 with the number of LPs on the n = 1008
+// workload at 1.5-2.5 dB). Key = complemented top bits of that sum | frame
+// index (24 bits), sorted ascending: the largest sums first, ties by index.
+constexpr unsigned long long kOrderIdx = (1ull << 24) - 1;
+
+__global__ void k_order_keys(const double* __restrict__ gamma, int n, int nframes, int n2,
+                             unsigned long long* keys) {
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int f = w; f < n2; f += nw) {
+        double s = 0.0;
+        if (f < nframes)
+            for (int i = lane; i < n; i += 32) {
+                const double g = gamma[(size_t)f * n + i];
+                s += g < 0.0 ? -g : 0.0;
+            }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0)
+            keys[f] = f < nframes
+                ? ((~((unsigned long long)__double_as_longlong(s) >> 24)) << 24) | (unsigned long long)f
+                : ~0ull;
+    }
+}
+
+// Bitonic sort of n2 (a power of two) keys in global memory by one CTA.
+__global__ void k_sort_keys(unsigned long long* key, int n2) {
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < (n2 >> 1); t += blockDim.x) {
+                const int i = 2 * t - (t & (j - 1));
+                const int l = i + j;
+                const bool up = (i & k) == 0;
+                const unsigned long long ki = key[i], kl = key[l];
+                if ((ki > kl) == up) { key[i] = kl; key[l] = ki; }
+            }
+            __syncthreads();
+        }
+}
+
 // Whole-frame decode. One code for every frame (descs == nullptr; frame f at
 // f*n / f*m), or per-frame codes from codes[descs[f].code] with ragged
 // offsets.
@@ -82,7 +126,7 @@ __global__ void __launch_bounds__(512)
 k_decode(CodeView C0, const CodeView* __restrict__ codes, const FrameDesc* __restrict__ descs,
          DevParams P, Layout L, Layout Lw, const double* __restrict__ gamma, double* u,
          uint8_t* hard, int32_t* cert, uint32_t* mask, lpdec_stats* stats, int nframes,
-         int* counter, char* gscratch) {
+         int* counter, char* gscratch, const unsigned long long* __restrict__ order) {
     KERNEL_PROLOGUE
     char* gw = gscratch + (size_t)blockIdx.x * L.stride + L.gbytes;   // wide workspace
     const Layout* lw = Lw.gbytes ? &Lw : nullptr;
@@ -91,6 +135,7 @@ k_decode(CodeView C0, const CodeView* __restrict__ codes, const FrameDesc* __res
     for (;;) {
         int f = next_frame(B, counter, &ks.next);
         if (f >= nframes) break;
+        if (order) f = (int)(order[f] & kOrderIdx);   // the queue's f-th frame
         long long on = (long long)f * C0.n, om = (long long)f * C0.m;
         if (descs) {
             const FrameDesc d = descs[f];
@@ -331,6 +376,8 @@ struct lpdec_ctx {
     char* h_meta = nullptr;      // ... and their pinned host copy
     size_t meta_bytes = 0;
     cudaEvent_t meta_done = nullptr;   // the last copy out of h_meta has run
+    unsigned long long* d_order = nullptr;   // frame order keys of a batch
+    size_t order_n = 0;
     std::mutex mu;
 };
 
@@ -556,9 +603,10 @@ size_t smem_budget_of(const lpdec_ctx* ctx) {
          : (third > per_cta ? std::min(cap, third - per_cta) : cap);
 }
 
+// Layout, CTA size and grid of a launch (no allocation); *per_sm = CTAs per SM.
 template <typename K>
-int32_t plan(lpdec_ctx* ctx, const Dims& dims, int nframes, K kernel, size_t real_bytes,
-             Launch* out) {
+int32_t shape(lpdec_ctx* ctx, const Dims& dims, int nframes, K kernel, size_t real_bytes,
+              Launch* out, int* per_sm_out) {
     int threads = ctx->prm.threads_per_block > 0 ? ctx->prm.threads_per_block : 128;
     threads = std::max(32, std::min(512, threads / 32 * 32));
     Layout L, Lw;
@@ -578,7 +626,22 @@ int32_t plan(lpdec_ctx* ctx, const Dims& dims, int nframes, K kernel, size_t rea
         snprintf(g_err, sizeof g_err, "kernel does not fit on an SM");
         return LPDEC_ERR_INVALID_ARG;
     }
-    int grid = std::max(1, std::min(nframes, per_sm * ctx->sm_count));
+    out->L = L;
+    out->Lw = Lw;
+    out->threads = threads;
+    out->grid = std::max(1, std::min(nframes, per_sm * ctx->sm_count));
+    *per_sm_out = per_sm;
+    return LPDEC_OK;
+}
+
+template <typename K>
+int32_t plan(lpdec_ctx* ctx, const Dims& dims, int nframes, K kernel, size_t real_bytes,
+             Launch* out) {
+    int per_sm = 0;
+    int32_t rc = shape(ctx, dims, nframes, kernel, real_bytes, out, &per_sm);
+    if (rc != LPDEC_OK) return rc;
+    const Layout& L = out->L;
+    const int grid = out->grid;
     // scratch for the full grid, whatever this batch needs, so that a small
     // batch (a warm-up) leaves no allocation to a later, larger one
     size_t need = (size_t)per_sm * ctx->sm_count * L.stride;
@@ -591,10 +654,6 @@ int32_t plan(lpdec_ctx* ctx, const Dims& dims, int nframes, K kernel, size_t rea
         CK(cudaMalloc(&ctx->gscratch, need));
         ctx->gscratch_bytes = need;
     }
-    out->L = L;
-    out->Lw = Lw;
-    out->threads = threads;
-    out->grid = grid;
     return LPDEC_OK;
 }
 
@@ -644,6 +703,13 @@ int32_t host_staging(lpdec_ctx* ctx, size_t bytes) {
     return LPDEC_OK;
 }
 
+// Whether a one-code batch of nframes on `grid` CTAs is handed out in the
+// hardest-first order (lpdec_params.order_frames).
+bool orders_frames(const lpdec_params& p, int nframes, int grid) {
+    return (p.order_frames == 2 || (p.order_frames == 1 && nframes > grid)) &&
+           nframes <= (int)kOrderIdx;
+}
+
 bool params_ok(const lpdec_params& p) {
     if (p.variant != LPDEC_MALP_A && p.variant != LPDEC_MALP_B && p.variant != LPDEC_ALP)
         return false;
@@ -653,6 +719,7 @@ bool params_ok(const lpdec_params& p) {
     if (p.lane_policy != 0 && p.lane_policy != 1 && p.lane_policy != 2 && p.lane_policy != 4 &&
         p.lane_policy != 8)
         return false;
+    if (p.order_frames < 0 || p.order_frames > 2) return false;
     return p.lp_rows_cap >= 0;
 }
 
@@ -676,15 +743,33 @@ int32_t launch_decode(lpdec_ctx* ctx, const lpdec_code* code, int nframes, const
     if (rc) return rc;
     const CodeView cv = view_of(code, ctx->prm);
     const DevParams dp = to_dev(ctx->prm);
+    // hardest-first frame order when frames queue behind the grid
+    const unsigned long long* order = nullptr;
+    if (orders_frames(ctx->prm, nframes, ln.grid)) {
+        int n2 = 1;
+        while (n2 < nframes) n2 <<= 1;
+        if ((size_t)n2 > ctx->order_n) {
+            if (ctx->d_order) CK(cudaFree(ctx->d_order));
+            ctx->d_order = nullptr;
+            ctx->order_n = 0;
+            CK(cudaMalloc(&ctx->d_order, (size_t)n2 * sizeof(unsigned long long)));
+            ctx->order_n = (size_t)n2;
+        }
+        k_order_keys<<<std::min(1024, (n2 + 7) / 8), 256, 0, s>>>(d_gamma, code->n, nframes, n2,
+                                                                 ctx->d_order);
+        k_sort_keys<<<1, 1024, 0, s>>>(ctx->d_order, n2);
+        CK(cudaGetLastError());
+        order = ctx->d_order;
+    }
     CK(cudaMemsetAsync(ctx->counter, 0, sizeof(int), s));
     if (mixed)
         k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
             cv, nullptr, nullptr, dp, ln.L, ln.Lw, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
-            nframes, ctx->counter, ctx->gscratch);
+            nframes, ctx->counter, ctx->gscratch, order);
     else
         k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
             cv, nullptr, nullptr, dp, ln.L, ln.Lw, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
-            nframes, ctx->counter, ctx->gscratch);
+            nframes, ctx->counter, ctx->gscratch, order);
     CK(cudaGetLastError());
     return LPDEC_OK;
 }
@@ -739,12 +824,12 @@ int32_t launch_decode_mixed(lpdec_ctx* ctx, int nframes, const lpdec_code* const
         k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
             views[0], dv, dd, dp, ln.L, ln.Lw, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
             nframes,
-            ctx->counter, ctx->gscratch);
+            ctx->counter, ctx->gscratch, nullptr);
     else
         k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
             views[0], dv, dd, dp, ln.L, ln.Lw, d_gamma, d_u, d_hard, d_cert, d_mask, d_stats,
             nframes,
-            ctx->counter, ctx->gscratch);
+            ctx->counter, ctx->gscratch, nullptr);
     CK(cudaGetLastError());
     return LPDEC_OK;
 }
@@ -780,6 +865,7 @@ void lpdec_default_params(lpdec_params* p) {
     p->warm_start = 0;
     p->mts_reuse = 0;
     p->lane_policy = 0;
+    p->order_frames = 1;
 }
 
 const char* lpdec_error_string(int32_t code) {
@@ -820,6 +906,25 @@ int32_t lpdec_workspace_bytes(int32_t m, int32_t n, int32_t E, int32_t precision
     if (L.smem_bytes == 0xffffffffu) return LPDEC_ERR_INVALID_ARG;
     if (smem_bytes) *smem_bytes = L.smem_bytes + sizeof(KernelShared);
     if (global_bytes_per_frame) *global_bytes_per_frame = (size_t)L.stride;
+    return LPDEC_OK;
+}
+
+int32_t lpdec_batch_grid(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
+                         int32_t* grid, int32_t* ordered) {
+    if (!ctx || !code || !grid || nframes < 0 || code->device != ctx->device)
+        return LPDEC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->device));
+    Dims d;
+    d.cover(view_of(code, ctx->prm));
+    Launch ln;
+    int per_sm = 0;
+    const bool mixed = ctx->prm.precision == LPDEC_MIXED;
+    int32_t rc = mixed ? shape(ctx, d, nframes, k_decode<float>, 4, &ln, &per_sm)
+                       : shape(ctx, d, nframes, k_decode<double>, 8, &ln, &per_sm);
+    if (rc != LPDEC_OK) return rc;
+    *grid = nframes > 0 ? ln.grid : 0;
+    if (ordered) *ordered = nframes > 0 && orders_frames(ctx->prm, nframes, ln.grid);
     return LPDEC_OK;
 }
 
@@ -874,6 +979,7 @@ void lpdec_ctx_destroy(lpdec_ctx* ctx) {
     cudaFree(ctx->staging);
     cudaFree(ctx->counter);
     cudaFree(ctx->d_meta);
+    cudaFree(ctx->d_order);
     cudaFreeHost(ctx->h_meta);
     cudaFreeHost(ctx->h_stage);
     if (ctx->meta_done) cudaEventDestroy(ctx->meta_done);
@@ -1391,12 +1497,12 @@ extern "C" int32_t lpdec_decode_batch_device_noalloc(const lpdec_code* code,
         k_decode<float><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
             view_of(code, prm), nullptr, nullptr, to_dev(prm), ln.L, ln.Lw, d_gamma, d_u, d_hard,
             d_cert, d_cut_mask, d_stats,
-            nframes, counter, gscratch);
+            nframes, counter, gscratch, nullptr);
     else
         k_decode<double><<<ln.grid, ln.threads, ln.L.smem_bytes, s>>>(
             view_of(code, prm), nullptr, nullptr, to_dev(prm), ln.L, ln.Lw, d_gamma, d_u, d_hard,
             d_cert, d_cut_mask, d_stats,
-            nframes, counter, gscratch);
+            nframes, counter, gscratch, nullptr);
     CK(cudaGetLastError());
     return LPDEC_OK;
 }

@@ -43,7 +43,7 @@ class lpdec_params(ctypes.Structure):
                [(k, ctypes.c_int32) for k in
                 ("max_alp", "max_ipm", "max_pcg", "variant", "precision",
                  "threads_per_block", "smem_budget", "lp_rows_cap", "precond",
-                 "precond_switch", "warm_start", "mts_reuse", "lane_policy", "reserved")]
+                 "precond_switch", "warm_start", "mts_reuse", "lane_policy", "order_frames")]
 
 
 class lpdec_stats(ctypes.Structure):
@@ -105,6 +105,7 @@ def _load():
     lib.lpdec_decode_mixed_device.argtypes = [P, i32, P, P, P, P, P, P, P, P]
     lib.lpdec_autotune.argtypes = [P, P, i32, P, ctypes.POINTER(i32), P]
     lib.lpdec_decode_batch_device.argtypes = [P, P, i32, P, P, P, P, P, P, P]
+    lib.lpdec_batch_grid.argtypes = [P, P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.lpdec_cut_search_device.argtypes = [P, P, i32, P, P, P, P, P, P]
     lib.lpdec_mts_select_device.argtypes = [P, P, i32, P, P, P, P, P, P, P]
     lib.lpdec_pcg_device.argtypes = [P, P, i32, P, P, P, P, P, P, P, P]
@@ -128,7 +129,7 @@ def _load():
         getattr(lib, name).restype = i32
     for name in ("lpdec_ctx_create", "lpdec_ctx_set_params", "lpdec_code_create",
                  "lpdec_decode", "lpdec_decode_batch", "lpdec_decode_frames", "lpdec_autotune",
-                 "lpdec_decode_mixed_device", "lpdec_decode_batch_device",
+                 "lpdec_decode_mixed_device", "lpdec_decode_batch_device", "lpdec_batch_grid",
                  "lpdec_cut_search_device", "lpdec_mts_select_device", "lpdec_pcg_device",
                  "lpdec_pcg_trace_device",
                  "lpdec_lp_solve_device", "lpdec_lp_solve_trace_device",
@@ -293,6 +294,14 @@ def lpdec_decode_batch_device(ctx, code, nframes, d_gamma, d_u, d_hard, d_cert,
     return _load().lpdec_decode_batch_device(ctx, code, nframes, _dptr(d_gamma), _dptr(d_u),
                                              _dptr(d_hard), _dptr(d_cert), _dptr(d_cut_mask),
                                              _dptr(d_stats), _stream(stream))
+
+
+def lpdec_batch_grid(ctx, code, nframes):
+    """(rc, grid, ordered): CTAs of a one-code batch of nframes, and whether
+    it is handed out hardest-first (two extra small kernels)."""
+    grid, ordered = ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = _load().lpdec_batch_grid(ctx, code, nframes, ctypes.byref(grid), ctypes.byref(ordered))
+    return rc, grid.value, ordered.value
 
 
 def lpdec_cut_search_device(ctx, code, nframes, d_u, d_active, d_in_lp, d_mask, d_flag,

@@ -103,6 +103,7 @@ def test_null_handles_rejected(lib):
     assert rc == L.LPDEC_ERR_INVALID_ARG
     rc = lib.lpdec_ctx_set_params(None, None)
     assert rc == L.LPDEC_ERR_INVALID_ARG
+    assert lib.lpdec_batch_grid(None, None, 1, None, None) == L.LPDEC_ERR_INVALID_ARG
 
 
 def test_server_reports_missing_device_and_null_handles(lib):

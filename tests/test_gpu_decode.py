@@ -314,3 +314,34 @@ def test_autotune_picks_a_schedule_and_decodes_exactly():
             u, hard, cert, masks, st = d.decode_batch(G)
         for f in range(60):
             compare_frame(ref[f], u[f], hard[f], cert[f], masks[f], st[f], f"policy {pol}, frame {f}")
+
+
+def test_frame_order_changes_start_times_not_results():
+    """order_frames = 2 hands out the frames with the largest sum of
+    -gamma_i over gamma_i < 0 first (they tend to need the most LPs), 0 in
+    the given order: the per-frame results are identical, and with many
+    more frames than CTAs the highest-sum frames start earlier."""
+    torch_cuda()
+    code = named_code("gallager_120")
+    G = awgn_llr_frames(code.n, code.design_rate, 1.5, 5, range(3000))
+    out = {}
+    for mode in (0, 1, 2):
+        prm = L.lpdec_default_params()
+        prm.order_frames = mode
+        with L.Decoder(code, params=prm) as d:
+            rc, grid, ordered = L.lpdec_batch_grid(d.ctx, d.code, len(G))
+            assert rc == 0 and 0 < grid < len(G) and ordered == (mode > 0)
+            assert L.lpdec_batch_grid(d.ctx, d.code, grid)[2] == (mode == 2)
+            out[mode] = d.decode_batch(G)
+    for mode in (1, 2):
+        for a, b in zip(out[0][:4], out[mode][:4]):
+            assert np.array_equal(a, b), mode
+        for fld in ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total", "lp_rows_final",
+                    "alp_switch", "objective"):
+            assert np.array_equal(out[0][4][fld], out[mode][4][fld]), (mode, fld)
+    key = np.where(G < 0, -G, 0.0).sum(axis=1)
+    rank = np.argsort(-key, kind="stable")
+    t = out[2][4]["t_start"]
+    assert np.mean(t[rank[:300]]) < np.mean(t[rank[-300:]])
+    t0 = out[0][4]["t_start"]
+    assert np.mean(t0[:300]) < np.mean(t0[-300:])
