@@ -439,6 +439,22 @@ def run_ours(args):
             "mean_ipm_iters_per_frame": float(st["ipm_iters_total"].mean()),
             "mean_pcg_iters_per_frame": float(st["pcg_iters_total"].mean()),
             "mean_dense_solves_per_frame": float(st["dense_solves"].mean()),
+            "ipm_iters_in_refinement_share": float(st["ipm_iters_refine"].sum()
+                                                   / max(1, st["ipm_iters_total"].sum())),
+            "lps_with_uncertified_vertex": int(st["vertex_failures"].sum()),
+            "phase_share_of_cta_time": {
+                k: float(st["sec_" + k].sum() / st["seconds"].sum())
+                for k in ("mts", "pcg", "dense", "certify", "refine")},
+            "slowest_frames": [
+                {"frame": int(frame_ids(nsteps - 1, rank, world, B_)[i]),
+                 "seconds": round(float(st["seconds"][i]), 3),
+                 **{k: int(st[k][i]) for k in ("status", "alp_iters", "ipm_iters_total",
+                                                "ipm_iters_refine", "pcg_iters_total",
+                                                "dense_solves", "lp_rows_max", "alp_switch",
+                                                "vertex_failures")},
+                 **{k: round(float(st[k][i]), 3) for k in ("sec_mts", "sec_pcg", "sec_dense",
+                                                            "sec_certify", "sec_refine")}}
+                for i in np.argsort(-st["seconds"])[:8]],
             "pcg_bytes_per_step": nbytes / args.steps,
             "pcg_flops_per_step": flops / args.steps,
             "fp64_tflops": flops / t_total / 1e12,

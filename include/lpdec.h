@@ -188,7 +188,8 @@ typedef struct lpdec_stats {
     int32_t dense_solves;     /* Newton systems solved by the dense Cholesky fallback */
     int32_t alp_switch;       /* LPs solved before a MALP frame continued as ALP (0: never) */
     int32_t lp_rows_max;      /* rows of the largest LP solved */
-    int32_t reserved;
+    int32_t ipm_iters_refine; /* of ipm_iters_total: iterations of the re-solves at a
+                                 tighter gap of LPs whose vertex failed the certificate */
     double  objective;        /* gamma'u */
     double  pcg_flops;        /* algorithmic floating-point operations of the Newton
                                  solves: PCG iterations (Q h, both triangular
@@ -202,6 +203,13 @@ typedef struct lpdec_stats {
                                  its two vectors, the two triangular solves
                                  (4 nnz(A_M) + 8p each) and five 8p vector passes */
     double  t_start, t_end;   /* device global timer (ns) at the frame's start and end */
+    /* device time (s) of the frame's phases, from the global timer: */
+    double  sec_mts;          /* triangular-set selections and their level schedules */
+    double  sec_pcg;          /* Newton solves by PCG (with FP64 refinement) */
+    double  sec_dense;        /* Newton solves that ended in the dense fallback */
+    double  sec_certify;      /* vertex certificates (basis and general) and recovery */
+    double  sec_refine;       /* re-solves at a tighter gap, all their phases included
+                                 (so overlapping the four above) */
 } lpdec_stats;
 
 typedef struct lpdec_ctx lpdec_ctx;    /* opaque: device, streams, scratch */

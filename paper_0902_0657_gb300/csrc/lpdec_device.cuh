@@ -359,6 +359,16 @@ __device__ __forceinline__ T signed_val(uint16_t ent, T v) { return (ent & kNeg)
 // ---------------------------------------------------------------------------
 // Frame state
 // ---------------------------------------------------------------------------
+// Device global timer (ns); the phase times of lpdec_stats.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ double since(unsigned long long t0) {
+    return 1e-9 * (double)(global_ns() - t0);
+}
+
 struct Frame {
     int p;          // LP rows
     int q;          // n + p
@@ -2119,6 +2129,7 @@ constexpr double kWarmFloor = 1e-2;
 struct IpmOut {
     int iters, pcg_iters, pcg_iters64, converged, certified, max_levels, dense;
     double flops, bytes;
+    double t_mts, t_pcg, t_dense, t_cert;   // phase times (s), lpdec_stats.sec_*
 };
 
 // trace (optional): per iteration 8 doubles {gap, feas_p, feas_d, PCG
@@ -2179,11 +2190,16 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Fram
             for (int i = B.tid; i < q; i += B.nt)
                 if (W.x[i] > W.zz[i]) { c0 += 1.0; c1 += (double)(i + 1) * (double)(i + 1); }
             double2 sg = bsum2(B, c0, c1);
-            if (sg.x == sig0 && sg.y == sig1 && certify<T>(B, C, W, F, gamma)) {
-                o.converged = 1;
-                o.certified = 1;
-                o.iters = it;
-                break;
+            if (sg.x == sig0 && sg.y == sig1) {
+                const unsigned long long tc = global_ns();
+                const int okc = certify<T>(B, C, W, F, gamma);
+                o.t_cert += since(tc);
+                if (okc) {
+                    o.converged = 1;
+                    o.certified = 1;
+                    o.iters = it;
+                    break;
+                }
             }
             sig0 = sg.x;
             sig1 = sg.y;
@@ -2235,14 +2251,21 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Fram
         // MTS reuse (lpdec_params.mts_reuse): keep the previous iteration's
         // triangular set while its PCG converged fast and the partition
         // x_i > z_i kept its size; the values of M (D_M^2) are always current
+        unsigned long long tp = global_ns();
         if (!(P.mts_reuse && reuse_ok)) L = select_mts<T>(B, C, W, F, W.d2, kind);
+        o.t_mts += since(tp);
         o.max_levels = max(o.max_levels, max(L.nb, L.nf));
         // near the optimum the selected basis may already be optimal
-        if (g_rel < P.tol_cert && certify_basis<T>(B, C, W, F, L, gamma)) {
-            o.converged = 1;
-            o.certified = 1;
-            o.iters = it;
-            break;
+        if (g_rel < P.tol_cert) {
+            tp = global_ns();
+            const int okb = certify_basis<T>(B, C, W, F, L, gamma);
+            o.t_cert += since(tp);
+            if (okb) {
+                o.converged = 1;
+                o.certified = 1;
+                o.iters = it;
+                break;
+            }
         }
         for (int i = B.tid; i < q; i += B.nt) W.d2t[i] = (T)W.d2[i];
         for (int r = B.tid; r < p; r += B.nt) {
@@ -2254,7 +2277,10 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Fram
         const double tol = fmax(P.tol_pcg, fmin(1e-3, P.pcg_gap_factor * g_rel));
         if (W.lz && B.tid == 0) { W.lz[2 * kLz] = 0.0; W.lz[2 * kLz + 1] = 0.0; }
         __syncthreads();
+        tp = global_ns();
         NewtonOut no = newton_solve<T>(B, C, W, F, L, P, tol, P.max_pcg, force64, force_dense);
+        if (no.dense) o.t_dense += since(tp);
+        else o.t_pcg += since(tp);
         o.dense += no.dense;
         o.pcg_iters += no.iters;
         o.pcg_iters64 += no.iters64;
@@ -2446,23 +2472,38 @@ __device__ inline bool solve_lp(Blk& B, const CodeView& C, WS<T>& W, Frame& F,
                                 IpmOut& io, bool warm = false, bool keep = false) {
     io = ipm_solve<T>(B, C, W, F, P, gamma, 0, nullptr, 0, warm);
     if (keep) save_iterate<T>(B, C, W, F);
+    unsigned long long tc = global_ns();
     int ok = io.certified || certify<T>(B, C, W, F, gamma);
+    io.t_cert += since(tc);
     DevParams Q = P;
     Q.max_ipm = 2 * P.max_ipm;
+    const unsigned long long tr = global_ns();
     for (int k = 0; k < 2 && !ok && io.converged; ++k) {
         Q.tol_gap = P.tol_gap * (k == 0 ? 1e-2 : 1e-3);
         IpmOut o2 = ipm_solve<T>(B, C, W, F, Q, gamma, 0);
+        st.ipm_iters_refine += o2.iters;
         o2.iters += io.iters;
         o2.pcg_iters += io.pcg_iters;
         o2.pcg_iters64 += io.pcg_iters64;
         o2.dense += io.dense;
         o2.flops += io.flops;
         o2.bytes += io.bytes;
+        o2.t_mts += io.t_mts;
+        o2.t_pcg += io.t_pcg;
+        o2.t_dense += io.t_dense;
+        o2.t_cert += io.t_cert;
         o2.max_levels = max(o2.max_levels, io.max_levels);
         io = o2;
+        tc = global_ns();
         ok = io.certified || certify<T>(B, C, W, F, gamma);
+        io.t_cert += since(tc);
+        if (ok || k == 1 || !io.converged) st.sec_refine += since(tr);
     }
-    if (!ok) st.vertex_failures += vertex_recover<T>(B, C, W, F, gamma);
+    if (!ok) {
+        tc = global_ns();
+        st.vertex_failures += vertex_recover<T>(B, C, W, F, gamma);
+        io.t_cert += since(tc);
+    }
     return io.converged || ok;
 }
 
@@ -2498,12 +2539,6 @@ __device__ inline double frame_cost(Blk& B, const CodeView& C, WS<T>& W, const d
     double a = 0.0;
     for (int i = B.tid; i < C.n; i += B.nt) a += gamma[i] * W.u[i];
     return bsum(B, a);
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
 }
 
 // Moves a frame's cut list to the wide workspace (Lw, at gw): the row-sized
@@ -2572,6 +2607,10 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, const WS<T>& W0,
         st.dense_solves += io.dense;
         st.pcg_flops += io.flops;
         st.pcg_bytes += io.bytes;
+        st.sec_mts += io.t_mts;
+        st.sec_pcg += io.t_pcg;
+        st.sec_dense += io.t_dense;
+        st.sec_certify += io.t_cert;
         st.max_levels = max(st.max_levels, io.max_levels);
         lp_finish<T>(B, C, W, F, P);
         st.lp_rows_final = F.p;

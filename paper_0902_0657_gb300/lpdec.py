@@ -50,17 +50,19 @@ class lpdec_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in
                 ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total", "lp_rows_final",
                  "vertex_failures", "max_levels", "pcg_iters_fp64", "dense_solves", "alp_switch",
-                 "lp_rows_max", "reserved")] + \
+                 "lp_rows_max", "ipm_iters_refine")] + \
                [(k, ctypes.c_double) for k in
-                ("objective", "pcg_flops", "seconds", "pcg_bytes", "t_start", "t_end")]
+                ("objective", "pcg_flops", "seconds", "pcg_bytes", "t_start", "t_end",
+                  "sec_mts", "sec_pcg", "sec_dense", "sec_certify", "sec_refine")]
 
 
 STATS_DTYPE = np.dtype([(k, np.int32) for k in
                         ("status", "alp_iters", "ipm_iters_total", "pcg_iters_total",
                          "lp_rows_final", "vertex_failures", "max_levels", "pcg_iters_fp64",
-                         "dense_solves", "alp_switch", "lp_rows_max", "reserved")] +
+                         "dense_solves", "alp_switch", "lp_rows_max", "ipm_iters_refine")] +
                        [(k, np.float64) for k in
-                        ("objective", "pcg_flops", "seconds", "pcg_bytes", "t_start", "t_end")])
+                        ("objective", "pcg_flops", "seconds", "pcg_bytes", "t_start", "t_end",
+                  "sec_mts", "sec_pcg", "sec_dense", "sec_certify", "sec_refine")])
 assert STATS_DTYPE.itemsize == ctypes.sizeof(lpdec_stats)
 
 

@@ -40,7 +40,8 @@ def test_all_declared_symbols_exported(lib):
 
 def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(L.lpdec_params) == 13 * 8 + 14 * 4
-    assert ctypes.sizeof(L.lpdec_stats) == 12 * 4 + 6 * 8
+    assert ctypes.sizeof(L.lpdec_stats) == 12 * 4 + 11 * 8
+    assert L.STATS_DTYPE.itemsize == ctypes.sizeof(L.lpdec_stats)
     p = L.lpdec_default_params()
     assert (p.sigma, p.eta, p.tol_gap, p.tol_feas) == (0.1, 0.99, 1e-8, 1e-8)
     assert (p.tau_act, p.tau_cut, p.tau_int, p.tau_inc) == (1e-9, 1e-9, 1e-9, 1e-9)
