@@ -105,8 +105,13 @@ def parse_args():
                     help="frames of the study checked against the full LP (HiGHS)")
     ap.add_argument("--max-pcg", type=int, default=0,
                     help="PCG iteration cap per Newton solve (0 = library default)")
-    ap.add_argument("--serve-frames", type=int, default=600,
-                    help="frames per load level of the serving workloads")
+    ap.add_argument("--sat-seconds", type=float, default=100.0,
+                    help="serving: length of the saturated run (rate over its last 60%%)")
+    ap.add_argument("--serve-seconds", type=float, default=45.0,
+                    help="serving: arrival window of each Poisson load level")
+    ap.add_argument("--serve-grace", type=float, default=60.0,
+                    help="serving: seconds after a level's last arrival before the frames "
+                         "still running are cancelled (their latency is reported as censored)")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0,
                     help="HBM admission budget of the serving workloads")
     return ap.parse_args()
@@ -505,12 +510,17 @@ def serving_frames(spec, codes, count, offset, seed=SEED):
 
 
 L_OUT_OF_BUDGET = -2   # lpdec.h LPDEC_ERR_OUT_OF_BUDGET
+L_CANCELLED = -8       # lpdec.h LPDEC_ERR_CANCELLED
+L_NOT_SERVED = -100    # (bench only) offered but never submitted
 
 
-def serve_run(srv, frames, rate=None):
+def serve_run(srv, frames, rate=None, stop_after=None):
     """Submits frames (as fast as admission allows if rate is None, else at
-    Poisson arrival times of that rate), polls them; returns (elapsed,
-    latencies in s, statuses)."""
+    Poisson arrival times of that rate) and polls them; at stop_after
+    seconds from the start, frames not finished are cancelled (running ones
+    stop at their next cancel check) and frames not yet submitted are
+    dropped. Returns (elapsed, latency in s or NaN if not served, finish
+    time from the start or NaN, status)."""
     import numpy as np
     import time as _t
     n = len(frames)
@@ -518,13 +528,20 @@ def serve_run(srv, frames, rate=None):
         arrive = np.zeros(n)
     else:
         arrive = np.cumsum(np.random.default_rng([SEED, 11, n]).exponential(1.0 / rate, n))
-    lat = np.zeros(n)
-    status = np.zeros(n, np.int32)
+    lat = np.full(n, np.nan)
+    fin = np.full(n, np.nan)
+    status = np.full(n, L_NOT_SERVED, np.int32)
     pending = {}
     k = 0
     t0 = _t.perf_counter()
     while k < n or pending:
         now = _t.perf_counter() - t0
+        if stop_after is not None and now > stop_after:
+            for t, (kk, ta) in pending.items():
+                srv.cancel(t)
+                status[kk] = L_CANCELLED
+            pending.clear()
+            break
         progressed = False
         while k < n and arrive[k] <= now:
             rc, t = srv.try_submit(frames[k][1], code=frames[k][0])
@@ -539,12 +556,27 @@ def serve_run(srv, frames, rate=None):
             r = srv.poll(t)
             if r is not None:
                 kk, ta = pending.pop(t)
-                lat[kk] = _t.perf_counter() - t0 - ta
+                fin[kk] = _t.perf_counter() - t0
+                lat[kk] = fin[kk] - ta
                 status[kk] = r[4]["status"]
                 progressed = True
         if not progressed:
             _t.sleep(0.0002)
-    return _t.perf_counter() - t0, lat, status
+    return _t.perf_counter() - t0, lat, fin, status
+
+
+def latency_summary(lat, offered):
+    """p50/p99/p99.9 in ms over the offered frames; a frame not served
+    (cancelled at the level's end, or never admitted) counts as slower than
+    every served one, and a percentile that falls on such frames is None."""
+    import numpy as np
+    x = np.where(np.isnan(lat), np.inf, lat)[:offered]
+    out = {}
+    for q, nm in ((50, "p50_ms"), (99, "p99_ms"), (99.9, "p99.9_ms")):
+        v = float(np.percentile(x, q, method="higher")) if len(x) else float("nan")
+        out[nm] = 1e3 * v if np.isfinite(v) else None
+    out["max_served_ms"] = 1e3 * float(np.nanmax(lat)) if np.any(~np.isnan(lat)) else None
+    return out
 
 
 def run_serving(args):
@@ -559,43 +591,62 @@ def run_serving(args):
     codes = [named_code(nm) for nm in spec["codes"]]
     prm = L.lpdec_default_params()
     prm.precision = {"fp64": L.LPDEC_FP64, "mixed": L.LPDEC_MIXED, "m32": L.LPDEC_M32}[args.precision]
-    N = args.serve_frames
     budget = int(args.serve_budget_gb * (1 << 30))
     levels = {}
-    with L.Server(codes, params=prm, hbm_budget_bytes=budget, max_pending=1 << 14) as srv:
-        warm = serving_frames(spec, codes, 64, 10 ** 6)
-        serve_run(srv, warm)
-        sat_frames = serving_frames(spec, codes, N, 0)
-        el, lat, st = serve_run(srv, sat_frames)
-        sat = N / el
-        print(f"[serving] saturated: {N} frames in {el:.1f} s", file=sys.stderr, flush=True)
-        levels["saturated"] = {"frames_per_s": sat, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                               "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                               "p99.9_ms": 1e3 * float(np.percentile(lat, 99.9)),
+    offset = 0
+
+    def frames_for(count):
+        nonlocal offset
+        fr = serving_frames(spec, codes, count, offset)
+        offset += count
+        return fr
+
+    with L.Server(codes, params=prm, hbm_budget_bytes=budget, max_pending=1 << 15) as srv:
+        serve_run(srv, serving_frames(spec, codes, 64, 10 ** 6), stop_after=60.0)   # warm-up
+        # saturated: more frames than the run can finish, all offered at once;
+        # the rate is taken over the last 60% of the run (the pipeline full)
+        T = args.sat_seconds
+        fr = frames_for(30000)
+        el, lat, fin, st = serve_run(srv, fr, stop_after=T)
+        w0 = 0.4 * T
+        sat = float(np.sum((fin >= w0) & (fin <= T))) / (T - w0)
+        print(f"[serving] saturated: {sat:.1f} frames/s over [{w0:.0f}, {T:.0f}] s",
+              file=sys.stderr, flush=True)
+        levels["saturated"] = {"frames_per_s": sat, "window_s": [w0, T],
+                               "frames_finished": int(np.sum(~np.isnan(fin))),
                                "frames_ok": int((st == 0).sum())}
-        for i, load in enumerate((0.5, 0.8, 0.95)):
-            fr = serving_frames(spec, codes, N, (i + 1) * N)
-            el, lat, st = serve_run(srv, fr, rate=load * sat)
-            print(f"[serving] load {load}: {N} frames in {el:.1f} s", file=sys.stderr, flush=True)
+        for load in (0.5, 0.8, 0.95):
+            rate = load * sat
+            cnt = max(1, int(rate * args.serve_seconds))
+            fr = frames_for(cnt)
+            el, lat, fin, st = serve_run(srv, fr, rate=rate,
+                                         stop_after=args.serve_seconds + args.serve_grace)
+            served = ~np.isnan(lat)
+            print(f"[serving] load {load}: {int(served.sum())}/{cnt} frames served",
+                  file=sys.stderr, flush=True)
             levels[f"poisson_{int(load * 100)}pct"] = {
-                "offered_frames_per_s": load * sat, "frames_per_s": N / el,
-                "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                "p99.9_ms": 1e3 * float(np.percentile(lat, 99.9)),
-                "frames_ok": int((st == 0).sum())}
+                "offered_frames_per_s": rate, "offered_frames": cnt,
+                "frames_per_s_served": float(served.sum()) / el,
+                **latency_summary(lat, cnt),
+                "frames_served": int(served.sum()), "frames_ok": int((st == 0).sum()),
+                "frames_cancelled_at_end": int((st == L_CANCELLED).sum())}
         hbm, arena, used, out = srv.stats()
     line = {
         "metric": f"served LP-decoded frames/s, {args.workload} mixed lengths; p50/p99/p99.9 latency",
         "value": sat, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {spec['what']}; {N} frames per load level "
-                               f"(the configuration's frame count scaled down to bound the run)",
+        "config": {"workload": f"{args.workload}: {spec['what']}; saturated for {args.sat_seconds:.0f} s, "
+                               f"then Poisson arrivals at 50/80/95% of that rate for "
+                               f"{args.serve_seconds:.0f} s each (frame counts scaled down from "
+                               f"the configuration's to bound the run)",
                    "codes": spec["codes"], "hbm_budget_gb": args.serve_budget_gb,
-                   "server_device_bytes": hbm, "precision": args.precision},
+                   "server_device_bytes": hbm, "precision": args.precision,
+                   "grace_s": args.serve_grace},
         "levels": levels,
         "latency": "host clock from a frame's arrival (its scheduled Poisson time) to the poll "
-                   "that returns its result",
+                   "that returns its result; frames still running grace_s after the last "
+                   "arrival are cancelled and count as slower than every served frame",
     }
     print(json.dumps(line), flush=True)
 

@@ -55,6 +55,7 @@ extern "C" {
 #define LPDEC_ERR_PENDING       -5  /* result not ready yet */
 #define LPDEC_ERR_CUDA          -6  /* a CUDA runtime call failed */
 #define LPDEC_ERR_NO_DEVICE     -7  /* no CUDA device / unsupported architecture */
+#define LPDEC_ERR_CANCELLED     -8  /* per frame (serving): cancelled while it ran */
 
 /* Adaptive-LP variants (Section III-A, Algorithm 1). */
 #define LPDEC_MALP_A 0
@@ -495,10 +496,13 @@ int32_t lpdec_submit(lpdec_server* server, const lpdec_code* code, const double*
 int32_t lpdec_poll(lpdec_server* server, uint64_t ticket, double* u_out, uint8_t* hard_out,
                    int32_t* cert_out, uint32_t* cut_mask_out, lpdec_stats* stats);
 
-/* Cancels a ticket: a frame no CTA has taken yet is skipped, a running one
- * runs to its end; either way its result is dropped and its region and
- * ticket are released (no poll needed). LPDEC_ERR_INVALID_ARG for a ticket
- * never issued, polled or cancelled. */
+/* Cancels a ticket: a frame no CTA has taken yet is skipped; a running one
+ * stops at its next check, one every four interior-point iterations and
+ * before each LP (milliseconds at the codes of the serving workloads), and
+ * frees its CTA for the next frame. Either way its result is dropped and
+ * its region and ticket are released once the CTA has let go of it (no
+ * poll needed). LPDEC_ERR_INVALID_ARG for a ticket never issued, polled or
+ * cancelled. */
 int32_t lpdec_cancel(lpdec_server* server, uint64_t ticket);
 
 /* Device bytes the server holds (scratch + arena), the arena's size, the

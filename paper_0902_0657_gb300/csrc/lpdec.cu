@@ -416,6 +416,7 @@ DevParams to_dev(const lpdec_params& p) {
     d.precond = p.precond; d.precond_switch = p.precond_switch;
     d.warm_start = p.warm_start; d.mts_reuse = p.mts_reuse;
     d.lane_policy = p.lane_policy;
+    d.abort = nullptr;
     return d;
 }
 
@@ -878,6 +879,7 @@ const char* lpdec_error_string(int32_t code) {
         case LPDEC_ERR_PENDING: return "pending";
         case LPDEC_ERR_CUDA: return g_err[0] ? g_err : "CUDA error";
         case LPDEC_ERR_NO_DEVICE: return "no usable CUDA device";
+        case LPDEC_ERR_CANCELLED: return "cancelled";
         default: return "unknown status";
     }
 }

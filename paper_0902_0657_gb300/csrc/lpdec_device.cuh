@@ -49,7 +49,17 @@ struct DevParams {
     int precond, precond_switch;
     int warm_start, mts_reuse;
     int lane_policy;
+    // serving: the frame's cancel flag in mapped host memory (null outside
+    // the server); read by thread 0 between LPs and every 4th IPM iteration
+    const volatile int32_t* abort;
 };
+
+// Whether the frame's cancel flag is set (the same value in every thread).
+__device__ __forceinline__ bool aborted(const DevParams& P) {
+    int a = 0;
+    if (P.abort && threadIdx.x == 0) a = *P.abort != 0;
+    return __syncthreads_or(a) != 0;
+}
 
 // ---------------------------------------------------------------------------
 // Workspace layout (the host decides shared vs global placement). Arrays over
@@ -2179,6 +2189,7 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Fram
     double nbasic_prev = -1.0;
     double prev_grel = INFINITY, sig0 = -1.0, sig1 = -1.0;
     for (int it = 0;; ++it) {
+        if (P.abort && (it & 3) == 3 && aborted(P)) { o.iters = it; break; }
         // Expensive regime (the basis certificate keeps failing and Newton
         // solves need hundreds of PCG iterations, typical of LPs with a
         // fractional optimum): below gap tol_cert, whenever the partition
@@ -2584,6 +2595,7 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, const WS<T>& W0,
     bool alp = P.variant == LPDEC_ALP;           // Algorithm 1 semantics
     for (;;) {
         if (P.variant == LPDEC_MALP_B && !alp) drop_inactive<T>(B, C, W);
+        if (P.abort && aborted(P)) { status = LPDEC_ERR_CANCELLED; break; }
         int added = cut_search<T>(B, C, W, P, alp);
         if (!added) break;
         if (st.alp_iters >= P.max_alp) { status = LPDEC_ERR_NOT_CONVERGED; break; }
@@ -2615,7 +2627,10 @@ __device__ inline void decode_frame(Blk& B, const CodeView& C, const WS<T>& W0,
         lp_finish<T>(B, C, W, F, P);
         st.lp_rows_final = F.p;
         st.lp_rows_max = max(st.lp_rows_max, F.p);
-        if (!solved) { status = LPDEC_ERR_NOT_CONVERGED; break; }
+        if (!solved) {
+            status = P.abort && aborted(P) ? LPDEC_ERR_CANCELLED : LPDEC_ERR_NOT_CONVERGED;
+            break;
+        }
         // Theorem 2(b): with unique LP optima the MALP cost rises strictly. A
         // cost that does not rise means that hypothesis failed and MALP may
         // cycle between cut sets short of the optimum; the frame continues as

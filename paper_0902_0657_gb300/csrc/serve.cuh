@@ -16,6 +16,8 @@
 //     entry points (so a result is the same alone and in the mix), writes
 //     the results into the region, and publishes completion in a mapped
 //     done flag after a system-scope fence;
+//   - a frame cancelled while it runs stops at its next check of the entry's
+//     cancel flag (between LPs, every fourth interior-point iteration);
 //   - a CTA that finds the queue empty waits, sleeping between looks, for at
 //     most idle_us of device time and then exits, so the kernel ends when the
 //     traffic stops; a host worker relaunches it when entries are waiting and
@@ -115,7 +117,9 @@ k_serve(const CodeView* __restrict__ codes, DevParams P, Layout L, Layout Lw, ch
                        reinterpret_cast<int32_t*>(base + rg.cert),
                        reinterpret_cast<uint32_t*>(base + rg.mask),
                        reinterpret_cast<lpdec_stats*>(base + rg.stats)};
-            decode_frame<T>(B, C, W, P, W.gam, o, 0, ks.shscan, lw, gw);
+            DevParams Pf = P;   // lpdec_cancel stops the frame while it runs
+            Pf.abort = &q[slot].cancel;
+            decode_frame<T>(B, C, W, Pf, W.gam, o, 0, ks.shscan, lw, gw);
         }
         __syncthreads();
         if (B.tid == 0) {

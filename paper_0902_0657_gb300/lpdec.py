@@ -24,6 +24,7 @@ LPDEC_ERR_TIMEOUT = -4
 LPDEC_ERR_PENDING = -5
 LPDEC_ERR_CUDA = -6
 LPDEC_ERR_NO_DEVICE = -7
+LPDEC_ERR_CANCELLED = -8
 LPDEC_MALP_A = 0
 LPDEC_MALP_B = 1
 LPDEC_ALP = 2

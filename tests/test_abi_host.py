@@ -93,6 +93,7 @@ def test_no_device_is_reported_not_emulated(lib):
         L.lpdec_ctx_create(0)
     assert e.value.code == L.LPDEC_ERR_NO_DEVICE
     assert L.error_string(L.LPDEC_ERR_NOT_CONVERGED) == "iteration cap reached"
+    assert L.error_string(L.LPDEC_ERR_CANCELLED) == "cancelled"
 
 
 def test_null_handles_rejected(lib):

@@ -4,7 +4,7 @@ code lengths. Frames submitted in waves while earlier ones run come back
 identical to the same frames decoded alone by the batch entry point; a
 frame submitted while a long batch runs is taken by a free CTA of the
 running kernel and finishes first; admission counts device-memory bytes;
-cancelled tickets are released."""
+cancelled tickets are released, and cancelled running frames stop."""
 
 import time
 
@@ -135,3 +135,40 @@ def test_cancel_releases_tickets_and_bytes():
             time.sleep(0.01)
         hbm, arena, used, out = srv.stats()
         assert used == 0 and out == 0
+
+
+def test_cancel_stops_running_frames():
+    """A cancelled frame that is running stops at its next check of the
+    cancel flag (between LPs, every fourth interior-point iteration): the
+    slowest frames of a 1.5 dB pool, seconds each when decoded, release
+    their CTAs and regions well within that time, and frames submitted
+    afterwards decode exactly as in a batch."""
+    torch_cuda()
+    c = named_code("peg_1008")
+    pool = awgn_llr_frames(c.n, c.design_rate, 1.5, 4, range(200))
+    key = np.where(pool < 0, -pool, 0.0).sum(axis=1)
+    hard = pool[np.argsort(-key)[:16]]
+    easy = awgn_llr_frames(c.n, c.design_rate, 3.0, 9, range(4))
+    with L.Decoder(c) as d:
+        st = d.decode_batch(hard)[4]
+        ue, he, ce, me, se = d.decode_batch(easy)
+    longest = float(st["seconds"].max())
+    assert longest > 2.0, longest   # (these frames do take seconds)
+    with L.Server([c]) as srv:
+        ts = [srv.submit(g) for g in hard]
+        time.sleep(0.5)
+        t0 = time.time()
+        for t in ts:
+            srv.cancel(t)
+        while srv.stats()[2] and time.time() - t0 < 120:
+            time.sleep(0.005)
+        released = time.time() - t0
+        hbm, arena, used, out = srv.stats()
+        assert used == 0 and out == 0
+        assert released < min(3.0, 0.5 * longest), (released, longest)
+        te = [srv.submit(g) for g in easy]
+        res = _wait(srv, te)
+    for k, t in enumerate(te):
+        u, h, cert, mask, s = res[t][0]
+        assert np.array_equal(h, he[k]) and cert == ce[k] and np.array_equal(u, ue[k])
+        assert np.array_equal(mask, me[k]) and s["status"] == se["status"][k]
