@@ -75,6 +75,9 @@ def parse_args():
                     help="1: interior-point warm start across the LPs of a frame")
     ap.add_argument("--mts-reuse", type=int, default=0,
                     help="1: reuse the triangular set across interior-point iterations")
+    ap.add_argument("--dense-switch", type=int, default=-1,
+                    help="PCG iterations after which an LP's Newton solves go dense "
+                         "(-1: library default, 0: only after a PCG stall)")
     ap.add_argument("--order", type=int, default=1,
                     help="frame order: 0 as given, 1 hardest first when frames queue (default), 2 always")
     ap.add_argument("--autotune", type=int, default=1,
@@ -126,6 +129,7 @@ def workload_config(args, n, m):
         "precision": args.precision, "smem_budget": args.smem_budget or "library (1/3 of SM)",
         "threads_per_block": args.threads, "variant": "MALP-A", "precond": args.precond,
         "warm_start": args.warm_start, "mts_reuse": args.mts_reuse, "order_frames": args.order,
+        "dense_switch": args.dense_switch if args.dense_switch >= 0 else "library default (64)",
         "l2": "flushed by a 256 MB write between timed steps",
     }
 
@@ -267,6 +271,8 @@ def run_ours(args):
     prm.warm_start = args.warm_start
     prm.mts_reuse = args.mts_reuse
     prm.order_frames = args.order
+    if args.dense_switch >= 0:
+        prm.dense_switch = args.dense_switch
     dec = L.Decoder(code, device=local, params=prm)
 
     tune = None

@@ -174,6 +174,13 @@ typedef struct lpdec_params {
                                    (largest sum of -gamma_i over gamma_i < 0), so the
                                    slow ones do not start last; 2 = always. Results do
                                    not depend on the order. */
+    int32_t dense_switch;       /* a Newton solve whose PCG converges after more than
+                                   this many iterations sends the rest of its LP's
+                                   Newton solves to the dense Cholesky fallback (when
+                                   the LP fits it); 0 = only after PCG stalls
+                                   (default 64: on GB300 a dense solve at m = 504 costs
+                                   about as much as that many PCG iterations) */
+    int32_t reserved;
 } lpdec_params;
 
 /* Per-frame results besides u / hard / cert. */

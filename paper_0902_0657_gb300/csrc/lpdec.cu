@@ -416,6 +416,7 @@ DevParams to_dev(const lpdec_params& p) {
     d.precond = p.precond; d.precond_switch = p.precond_switch;
     d.warm_start = p.warm_start; d.mts_reuse = p.mts_reuse;
     d.lane_policy = p.lane_policy;
+    d.dense_switch = p.dense_switch;
     d.abort = nullptr;
     return d;
 }
@@ -721,6 +722,7 @@ bool params_ok(const lpdec_params& p) {
         p.lane_policy != 8)
         return false;
     if (p.order_frames < 0 || p.order_frames > 2) return false;
+    if (p.dense_switch < 0) return false;
     return p.lp_rows_cap >= 0;
 }
 
@@ -867,6 +869,8 @@ void lpdec_default_params(lpdec_params* p) {
     p->mts_reuse = 0;
     p->lane_policy = 0;
     p->order_frames = 1;
+    p->dense_switch = 64;
+    p->reserved = 0;
 }
 
 const char* lpdec_error_string(int32_t code) {

@@ -49,6 +49,7 @@ struct DevParams {
     int precond, precond_switch;
     int warm_start, mts_reuse;
     int lane_policy;
+    int dense_switch;
     // serving: the frame's cancel flag in mapped host memory (null outside
     // the server); read by thread 0 between LPs and every 4th IPM iteration
     const volatile int32_t* abort;
@@ -1752,20 +1753,63 @@ __device__ inline int refine_round(Blk& B, const CodeView& C, WS<V>& WV, WS<T>& 
 }
 
 // Fallback Newton solve (A D^2 A') dy = w by a dense FP64 Cholesky
-// factorization Q = L L' (column-major, in W.qd), for the systems on which
-// PCG stalls (large degenerate LPs near the optimum, where the MTS
-// preconditioner of Section V no longer captures Q). This is the direct
-// method of the normal equations (Eq. 24); it leaves dy untouched and
-// returns false if Q has a non-finite entry or a non-positive diagonal.
+// factorization Q = L L' (column-major, leading dimension p, in W.qd), for
+// the systems on which PCG stalls or runs long (large degenerate LPs near
+// the optimum, where the MTS preconditioner of Section V no longer captures
+// Q). This is the direct method of the normal equations (Eq. 24); it leaves
+// dy untouched and returns false if Q has a non-finite entry or a
+// non-positive diagonal.
+//
+// Blocked right-looking factorization, panels of kDB = 32 columns: the
+// panel's diagonal block is factored by one warp; the rows below it are
+// solved against that block, one row per thread (32 values in registers);
+// the trailing lower triangle is updated in 4 x 4 register tiles, one tile
+// per thread at a time, reading the panel from L2 (consecutive threads take
+// consecutive row tiles of one column tile, so the loads coalesce). The two
+// triangular solves go panel by panel as well: one warp solves the 32 x 32
+// diagonal block, then every thread updates its rows. Each panel costs a
+// few CTA barriers instead of one or two per column.
 constexpr double kPivotTiny = 1e-13;
 constexpr double kPivotHuge = 1e64;
+constexpr int kDB = 32;
+
+// Factors columns k0 .. k0+kb-1 of the diagonal block in place (one warp;
+// lane l holds row k0+j+1+l of column j). The original diagonal of column
+// j >= 1 is kept at (j-1, j), in the unused upper triangle. Returns true
+// (same in every lane) if a diagonal entry is non-finite or not positive.
+__device__ __forceinline__ bool chol_diag_block(double* A, int p, int k0, int kb, int lane) {
+    bool bad = false;
+    for (int j = 0; j < kb; ++j) {
+        const int jj = k0 + j;
+        double* colj = A + (size_t)jj * p;
+        const double sjj = colj[jj];
+        const double qjj = jj == 0 ? sjj : colj[jj - 1];
+        bad = bad || !isfinite(sjj) || !(qjj > 0.0);
+        // A pivot at the rounding level of Q(j,j) means Q is singular to
+        // working precision along y_j (a degenerate optimum): it is given a
+        // huge value, which zeroes that component of the step instead of
+        // amplifying rounding noise (the usual treatment of tiny pivots in
+        // interior-point normal equations).
+        const bool tiny = !(sjj > kPivotTiny * qjj);
+        const double ljj = tiny ? kPivotHuge : sqrt(sjj), inv = 1.0 / ljj;
+        const int i = jj + 1 + lane;
+        double lij = 0.0;
+        if (i < k0 + kb) { lij = colj[i] * inv; colj[i] = lij; }
+        __syncwarp();
+        if (lane == 0) colj[jj] = ljj;
+        if (i < k0 + kb)
+            for (int l = jj + 1; l <= i; ++l) A[(size_t)l * p + i] -= lij * colj[l];
+        __syncwarp();
+    }
+    return bad;
+}
 
 template <typename T>
 __device__ __noinline__ bool dense_newton(Blk& B, const CodeView C, WS<T> W, const Frame& F) {
     const int n = C.n, p = F.p;
-    double* Lm = W.qd;
+    double* A = W.qd;
     const size_t pp = (size_t)p * p;
-    for (size_t k = B.tid; k < pp; k += B.nt) Lm[k] = 0.0;
+    for (size_t k = B.tid; k < pp; k += B.nt) A[k] = 0.0;
     __syncthreads();
     // Q(r, r2) = sum over the standard columns i of rows r, r2 of
     // A(r,i) A(r2,i) d_i^2, plus d^2 of row r's slack on the diagonal; thread
@@ -1778,52 +1822,130 @@ __device__ __noinline__ bool dense_newton(Blk& B, const CodeView C, WS<T> W, con
             for (uint32_t k = W.cptr[i]; k < W.cptr[i + 1]; ++k) {
                 const uint16_t ce = W.colent[k];
                 const int r2 = ce & kIdx;
-                Lm[(size_t)r2 * p + r] += ((ent ^ ce) & kNeg) ? -dd : dd;
+                A[(size_t)r2 * p + r] += ((ent ^ ce) & kNeg) ? -dd : dd;
             }
         }
-        Lm[(size_t)r * p + r] += W.d2[n + r];
+        A[(size_t)r * p + r] += W.d2[n + r];
     }
     __syncthreads();
-    // left-looking Cholesky, one column per step
-    for (int j = 0; j < p; ++j) {
-        double part = 0.0;
-        for (int k = B.tid; k < j; k += B.nt) {
-            const double v = Lm[(size_t)k * p + j];
-            part += v * v;
+    for (int j = 1 + B.tid; j < p; j += B.nt) A[(size_t)j * p + j - 1] = A[(size_t)j * p + j];
+    __syncthreads();
+    const bool sweeper = B.warp == B.sw;
+    for (int k0 = 0; k0 < p; k0 += kDB) {
+        const int kb = min(kDB, p - k0);
+        int bad = 0;
+        if (sweeper) bad = chol_diag_block(A, p, k0, kb, B.lane);
+        if (__syncthreads_or(bad)) return false;   // (same value in every thread)
+        const int r0 = k0 + kDB;
+        if (r0 >= p) break;
+        // rows below: x = a L11^-T, one row per thread (kb = kDB here)
+        for (int i = r0 + B.tid; i < p; i += B.nt) {
+            double x[kDB];
+#pragma unroll
+            for (int t = 0; t < kDB; ++t) x[t] = A[(size_t)(k0 + t) * p + i];
+#pragma unroll
+            for (int t = 0; t < kDB; ++t) {
+                const double* ct = A + (size_t)(k0 + t) * p + k0;   // column k0+t of the block
+                double v = x[t];
+#pragma unroll
+                for (int s2 = 0; s2 < t; ++s2) v -= x[s2] * A[(size_t)(k0 + s2) * p + k0 + t];
+                x[t] = v / ct[t];
+            }
+#pragma unroll
+            for (int t = 0; t < kDB; ++t) A[(size_t)(k0 + t) * p + i] = x[t];
         }
-        const double qjj = Lm[(size_t)j * p + j];
-        const double sjj = qjj - bsum(B, part);
-        if (!isfinite(sjj) || !(qjj > 0.0)) return false;   // same values in every thread
-        // A pivot at the rounding level of Q(j,j) means Q is singular to
-        // working precision along y_j (a degenerate optimum): it is given a
-        // huge value, which zeroes that component of the step instead of
-        // amplifying rounding noise (the usual treatment of tiny pivots in
-        // interior-point normal equations).
-        const bool tiny = !(sjj > kPivotTiny * qjj);
-        const double ljj = tiny ? kPivotHuge : sqrt(sjj), inv = 1.0 / ljj;
-        for (int i = j + 1 + B.tid; i < p; i += B.nt) {
-            double acc = Lm[(size_t)j * p + i];
-            for (int k = 0; k < j; ++k) acc -= Lm[(size_t)k * p + i] * Lm[(size_t)k * p + j];
-            Lm[(size_t)j * p + i] = acc * inv;
+        __syncthreads();
+        // trailing lower triangle -= L21 L21', 4 x 4 tiles (bi >= bj),
+        // enumerated column tile by column tile
+        const int m2 = p - r0, nb4 = (m2 + 3) >> 2;
+        const int ntile = nb4 * (nb4 + 1) / 2;
+        for (int b = B.tid; b < ntile; b += B.nt) {
+            // column tile bj: tiles bj..nb4-1, starting at off(bj) = bj nb4 - bj (bj - 1) / 2
+            int bj = (int)((2.0 * nb4 + 1.0 - sqrt((2.0 * nb4 + 1.0) * (2.0 * nb4 + 1.0) - 8.0 * b)) * 0.5);
+            bj = max(0, min(bj, nb4 - 1));
+            while (bj > 0 && bj * nb4 - bj * (bj - 1) / 2 > b) --bj;
+            while (bj + 1 < nb4 && (bj + 1) * nb4 - (bj + 1) * bj / 2 <= b) ++bj;
+            const int bi = bj + (b - (bj * nb4 - bj * (bj - 1) / 2));
+            const int i0 = r0 + 4 * bi, j0 = r0 + 4 * bj;
+            double acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+            for (int t = 0; t < kDB; ++t) {
+                const double* ct = A + (size_t)(k0 + t) * p;
+                double li[4], lj[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    li[a] = i0 + a < p ? ct[i0 + a] : 0.0;
+                    lj[a] = j0 + a < p ? ct[j0 + a] : 0.0;
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][c] = fma(li[a], lj[c], acc[a][c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = j0 + c;
+                if (j >= p) continue;
+                double* cj = A + (size_t)j * p;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int i = i0 + a;
+                    if (i < p && i >= j) cj[i] -= acc[a][c];
+                }
+            }
         }
-        if (B.tid == 0) Lm[(size_t)j * p + j] = ljj;
         __syncthreads();
     }
-    // L y = w (y into dy), then L' dy = y
+    // L y = w (into r64), panel by panel
     for (int r = B.tid; r < p; r += B.nt) W.r64[r] = W.w[r];
     __syncthreads();
-    for (int j = 0; j < p; ++j) {
-        const double yj = W.r64[j] / Lm[(size_t)j * p + j];
-        for (int i = j + 1 + B.tid; i < p; i += B.nt) W.r64[i] -= Lm[(size_t)j * p + i] * yj;
-        if (B.tid == 0) W.dy[j] = yj;
+    for (int k0 = 0; k0 < p; k0 += kDB) {
+        const int kb = min(kDB, p - k0);
+        if (sweeper)
+            for (int j = k0; j < k0 + kb; ++j) {
+                const double* cj = A + (size_t)j * p;
+                const double yj = W.r64[j] / cj[j];
+                __syncwarp();
+                const int i = j + 1 + B.lane;
+                if (i < k0 + kb) W.r64[i] -= cj[i] * yj;
+                if (B.lane == 0) W.r64[j] = yj;
+                __syncwarp();
+            }
+        __syncthreads();
+        for (int i = k0 + kb + B.tid; i < p; i += B.nt) {
+            double v = W.r64[i];
+            for (int t = 0; t < kb; ++t) v -= A[(size_t)(k0 + t) * p + i] * W.r64[k0 + t];
+            W.r64[i] = v;
+        }
         __syncthreads();
     }
-    for (int j = p - 1; j >= 0; --j) {
-        double part = 0.0;
-        for (int i = j + 1 + B.tid; i < p; i += B.nt) part += Lm[(size_t)j * p + i] * W.dy[i];
-        const double yj = W.dy[j];
-        const double sum = bsum(B, part);
-        if (B.tid == 0) W.dy[j] = (yj - sum) / Lm[(size_t)j * p + j];
+    // L' dy = y, panel by panel from the last
+    for (int r = B.tid; r < p; r += B.nt) W.dy[r] = W.r64[r];
+    __syncthreads();
+    for (int k0 = ((p - 1) / kDB) * kDB; k0 >= 0; k0 -= kDB) {
+        const int kb = min(kDB, p - k0);
+        if (sweeper)
+            for (int j = k0 + kb - 1; j >= k0; --j) {
+                const double* cj = A + (size_t)j * p;
+                // dy_j = (y_j - sum_{j < i < k0+kb} L(i,j) dy_i) / L(j,j)
+                const int i = j + 1 + B.lane;
+                double part = i < k0 + kb ? cj[i] * W.dy[i] : 0.0;
+                const double sum = warp_sum(part);
+                __syncwarp();
+                if (B.lane == 0) W.dy[j] = (W.dy[j] - sum) / cj[j];
+                __syncwarp();
+            }
+        __syncthreads();
+        // rows above the panel: dy_i -= sum_t L(k0+t, i) dy_{k0+t}
+        for (int i = B.tid; i < k0; i += B.nt) {
+            const double* ci = A + (size_t)i * p + k0;
+            double v = W.dy[i];
+            for (int t = 0; t < kb; ++t) v -= ci[t] * W.dy[k0 + t];
+            W.dy[i] = v;
+        }
         __syncthreads();
     }
     return true;
@@ -1901,6 +2023,10 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
         }
     }
     o.relres = rn / wn;
+    // PCG that converged but ran long (lpdec_params.dense_switch): the later
+    // Newton systems of this LP only get harder, so they go to the direct
+    // solve, cheaper than that many PCG iterations
+    if (dense_ok && P.dense_switch > 0 && o.iters > P.dense_switch) force_dense = true;
     if (o.relres > tol && dense_ok) {   // PCG stalled: direct solve, for the rest of the LP
         force_dense = true;
         if (dense_newton<T>(B, C, W, F)) {

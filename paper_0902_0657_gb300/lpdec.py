@@ -44,7 +44,8 @@ class lpdec_params(ctypes.Structure):
                [(k, ctypes.c_int32) for k in
                 ("max_alp", "max_ipm", "max_pcg", "variant", "precision",
                  "threads_per_block", "smem_budget", "lp_rows_cap", "precond",
-                 "precond_switch", "warm_start", "mts_reuse", "lane_policy", "order_frames")]
+                 "precond_switch", "warm_start", "mts_reuse", "lane_policy", "order_frames",
+                 "dense_switch", "reserved")]
 
 
 class lpdec_stats(ctypes.Structure):

@@ -39,7 +39,7 @@ def test_all_declared_symbols_exported(lib):
 
 
 def test_struct_sizes_match_header(lib):
-    assert ctypes.sizeof(L.lpdec_params) == 13 * 8 + 14 * 4
+    assert ctypes.sizeof(L.lpdec_params) == 13 * 8 + 16 * 4
     assert ctypes.sizeof(L.lpdec_stats) == 12 * 4 + 11 * 8
     assert L.STATS_DTYPE.itemsize == ctypes.sizeof(L.lpdec_stats)
     p = L.lpdec_default_params()
@@ -47,6 +47,7 @@ def test_struct_sizes_match_header(lib):
     assert (p.tau_act, p.tau_cut, p.tau_int, p.tau_inc) == (1e-9, 1e-9, 1e-9, 1e-9)
     assert (p.max_alp, p.max_ipm, p.max_pcg, p.variant, p.precision) == (200, 60, 1000, 0, 0)
     assert p.lp_rows_cap == 0
+    assert (p.order_frames, p.dense_switch, p.reserved) == (1, 64, 0)
 
 
 @pytest.mark.parametrize("name", ["gallager_120", "peg_1008", "gallager_504", "gallager_4032",

@@ -53,12 +53,18 @@ def test_golden_file_covers_the_workload():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", [L.LPDEC_FP64, L.LPDEC_M32, L.LPDEC_MIXED])
-def test_full_size_matches_oracle_goldens(precision):
+@pytest.mark.parametrize("precision,dense_switch", [
+    (L.LPDEC_FP64, 64), (L.LPDEC_M32, 64), (L.LPDEC_MIXED, 64),
+    (L.LPDEC_FP64, 0), (L.LPDEC_FP64, 1)])
+def test_full_size_matches_oracle_goldens(precision, dense_switch):
+    """Every precision mode with the default switch to the dense solve,
+    and FP64 with PCG until it stalls (0) or the dense solve for almost
+    every Newton system (1)."""
     torch = torch_cuda()
     code, seed, rows = load()
     prm = L.lpdec_default_params()
     prm.precision = precision
+    prm.dense_switch = dense_switch
     worst_u = 0.0
     failures = []
     with L.Decoder(code, params=prm) as d:
@@ -98,5 +104,6 @@ def test_full_size_matches_oracle_goldens(precision):
                         bad.append(f"{fld} {st[fld][k]} vs {r[fld]}")
                 if bad:
                     failures.append((ctx, bad))
-    print(f"precision {precision}: max |u - u_oracle| = {worst_u:.3e}")
+    print(f"precision {precision}, dense_switch {dense_switch}: "
+          f"max |u - u_oracle| = {worst_u:.3e}")
     assert not failures, failures
