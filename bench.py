@@ -874,6 +874,8 @@ def run_x123(args):
                                 "p95_lps": float(np.sort(lps[sel])[int(np.ceil(0.95 * sel.sum())) - 1]),
                                 "mean_largest_lp_rows": float(st["lp_rows_max"][sel].mean())}
             ent["frames_ok"] = int((st["status"] == 0).sum())
+            ent["status_counts"] = {str(int(k)): int(v) for k, v in
+                                    zip(*np.unique(st["status"], return_counts=True))}
             ent["frames_switched_to_alp"] = int((st["alp_switch"] > 0).sum())
             row[name] = ent
             largest[name] = st["lp_rows_max"].astype(float), integ

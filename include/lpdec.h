@@ -175,10 +175,12 @@ typedef struct lpdec_params {
                                    slow ones do not start last; 2 = always. Results do
                                    not depend on the order. */
     int32_t dense_switch;       /* a Newton solve whose PCG converges after more than
-                                   this many iterations sends the rest of its LP's
-                                   Newton solves to the dense Cholesky fallback (when
-                                   the LP fits it); 0 = only after PCG stalls
-                                   (default 64: on GB300 a dense solve at m = 504 costs
+                                   max(16, dense_switch (p/512)^2) iterations (p the
+                                   LP's rows) sends the rest of its LP's Newton solves
+                                   to the dense Cholesky fallback (when the LP fits
+                                   it); 0 = only after PCG stalls. A dense solve costs
+                                   p^3/6 FMAs, a PCG iteration about p dependent steps;
+                                   default 64 (on GB300 a dense solve at 512 rows costs
                                    about as much as that many PCG iterations) */
     int32_t reserved;
 } lpdec_params;

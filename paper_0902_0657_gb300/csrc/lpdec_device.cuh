@@ -2025,8 +2025,12 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
     o.relres = rn / wn;
     // PCG that converged but ran long (lpdec_params.dense_switch): the later
     // Newton systems of this LP only get harder, so they go to the direct
-    // solve, cheaper than that many PCG iterations
-    if (dense_ok && P.dense_switch > 0 && o.iters > P.dense_switch) force_dense = true;
+    // solve, cheaper than that many PCG iterations. A dense solve costs
+    // p^3/6 FMAs, a PCG iteration about p sequential steps: the threshold is
+    // dense_switch at 512 rows, scaled by (p/512)^2, and at least 16.
+    if (dense_ok && P.dense_switch > 0 &&
+        o.iters > fmax(16.0, P.dense_switch * ((double)p * p) / (512.0 * 512.0)))
+        force_dense = true;
     if (o.relres > tol && dense_ok) {   // PCG stalled: direct solve, for the rest of the LP
         force_dense = true;
         if (dense_newton<T>(B, C, W, F)) {

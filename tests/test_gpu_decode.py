@@ -42,7 +42,8 @@ def test_decode_gallager120_200_frames(precision, threads, precond):
     precision (FP32 PCG refined against FP64 residuals) and with the FP32
     preconditioner solve, at several CTA sizes, and with each of the
     triangular-set preconditioners of Section V (they change the PCG
-    iterations, not the LP solutions)."""
+    iterations, not the LP solutions), with PCG kept for every Newton system
+    it solves (no early switch to the dense solve)."""
     torch_cuda()
     code = named_code("gallager_120")
     G = awgn_llr_frames(code.n, code.design_rate, 2.0, 0, range(200))
@@ -51,6 +52,7 @@ def test_decode_gallager120_200_frames(precision, threads, precond):
     prm.threads_per_block = threads
     prm.precond = precond
     prm.precond_switch = 20   # (n = 120: switch early enough to be exercised)
+    prm.dense_switch = 0      # (PCG for every Newton solve that converges)
     with L.Decoder(code, params=prm) as d:
         u, hard, cert, masks, st = d.decode_batch(G)
     n_frac = 0
