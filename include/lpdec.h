@@ -175,7 +175,7 @@ typedef struct lpdec_params {
                                    slow ones do not start last; 2 = always. Results do
                                    not depend on the order. */
     int32_t dense_switch;       /* a Newton solve whose PCG converges after more than
-                                   max(16, dense_switch (p/512)^2) iterations (p the
+                                   dense_switch max(1, (p/512)^2) iterations (p the
                                    LP's rows) sends the rest of its LP's Newton solves
                                    to the dense Cholesky fallback (when the LP fits
                                    it); 0 = only after PCG stalls. A dense solve costs

@@ -1872,6 +1872,7 @@ __device__ __noinline__ bool dense_newton(Blk& B, const CodeView C, WS<T> W, con
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+#pragma unroll 4
             for (int t = 0; t < kDB; ++t) {
                 const double* ct = A + (size_t)(k0 + t) * p;
                 double li[4], lj[4];
@@ -2026,10 +2027,11 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
     // PCG that converged but ran long (lpdec_params.dense_switch): the later
     // Newton systems of this LP only get harder, so they go to the direct
     // solve, cheaper than that many PCG iterations. A dense solve costs
-    // p^3/6 FMAs, a PCG iteration about p sequential steps: the threshold is
-    // dense_switch at 512 rows, scaled by (p/512)^2, and at least 16.
+    // p^3/6 FMAs, a PCG iteration about p sequential steps: above 512 rows
+    // the threshold grows as (p/512)^2 (below, fixed costs of both keep it
+    // flat).
     if (dense_ok && P.dense_switch > 0 &&
-        o.iters > fmax(16.0, P.dense_switch * ((double)p * p) / (512.0 * 512.0)))
+        o.iters > P.dense_switch * fmax(1.0, ((double)p * p) / (512.0 * 512.0)))
         force_dense = true;
     if (o.relres > tol && dense_ok) {   // PCG stalled: direct solve, for the rest of the LP
         force_dense = true;
