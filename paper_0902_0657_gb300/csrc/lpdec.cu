@@ -494,7 +494,8 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
     const size_t q = (size_t)n + pm;
     size_t q2 = 1;
     while (q2 < q) q2 <<= 1;
-    const size_t vec = std::max(vec_bytes(n, pm, real_bytes, m32), 12 * q2 + 4 * q);
+    const size_t vec = vec_hot_bytes(n, pm, real_bytes, m32);
+    const size_t vecc = vec_cold_bytes(n, pm, real_bytes, q2);
     struct Spec { int id; size_t bytes; int where; };  // 0 = budgeted, 1 = always shared, 2 = global
     const size_t D = 8, I = 4, H = 2, P = (size_t)pm;
     std::vector<Spec> specs = {
@@ -502,20 +503,23 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
         {S_CUR, I * (P + 2), 1},
         // budgeted arrays in priority order: first what every PCG iteration
         // reads on its serial path (the two level-scheduled triangular
-        // solves), then the sparse passes of Q h, then what runs once per
-        // interior-point iteration (MTS selection, level build), then the
-        // cut search and the cut list
+        // solves: values, dependency lists and ranges, level rows, pivot
+        // signs), then what the serial greedy of the MTS selection walks
+        // once per interior-point iteration (pivots, degrees, levels, the
+        // column and row entries of A), then the rest of the sparse passes
+        // and the level build, then the cut search and the cut list, and
+        // last the vectors of the parallel passes of Q h (and sort keys)
         {S_VEC, vec, 0}, {S_BDEP, H * ea, 0}, {S_FDEP, H * ea, 0}, {S_LBSE, 8 * P, 0},
-        {S_LFSE, 8 * P, 0}, {S_LBROWS, H * P, 0}, {S_LFROWS, H * P, 0},
+        {S_LFSE, 8 * P, 0}, {S_LBROWS, H * P, 0}, {S_LFROWS, H * P, 0}, {S_PSGN, P, 0},
+        {S_PIVCOL, H * P, 0}, {S_PIVROW, H * q, 0}, {S_LF, H * P, 0}, {S_LB, H * P, 0},
+        {S_DEG, H * q, 0}, {S_SELROW, H * P, 0},
+        {S_CPTR, I * ((size_t)n + 1), 0}, {S_ROWENT, H * ea, 0}, {S_RPTR, I * (P + 1), 0},
+        {S_COLENT, H * ea, 0},
         {S_BPTR, I * (P + 1), 0}, {S_FPTR, I * (P + 1), 0},
-        {S_PSGN, P, 0}, {S_ROWENT, H * ea, 0}, {S_RPTR, I * (P + 1), 0},
-        {S_COLENT, H * ea, 0}, {S_CPTR, I * ((size_t)n + 1), 0},
-        {S_PIVROW, H * q, 0}, {S_PIVCOL, H * P, 0}, {S_LB, H * P, 0},
-        {S_LF, H * P, 0}, {S_SELROW, H * P, 0}, {S_DEG, H * q, 0},
         {S_HPTR, I * ((size_t)m + 1), 0}, {S_VPTR, I * ((size_t)n + 1), 0},
         {S_CCHK, H * P, 0}, {S_CRPTR, I * ((size_t)m + 1), 0}, {S_FLAGS, (size_t)m, 0},
         {S_MASK, I * (size_t)m, 0}, {S_CMASK, I * P, 0}, {S_CACT, P, 0},
-        {S_FLIP, I * (((size_t)n + 31) / 32), 0},
+        {S_FLIP, I * (((size_t)n + 31) / 32), 0}, {S_VECC, vecc, 0},
         {G_X, D * q, 2}, {G_Z, D * q, 2}, {G_RC, D * q, 2}, {G_D2, D * q, 2}, {G_Y, D * P, 2},
         {G_B, D * P, 2}, {G_W, D * P, 2}, {G_DY, D * P, 2}, {G_R64, D * P, 2}, {G_U, D * n, 2},
         {G_T64, D * n, 2}, {G_BASIC, q, 2},
