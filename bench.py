@@ -44,6 +44,13 @@ SEED = 0
 FP64_FLOPS_PER_SM_CLK = 4.0
 N_SMS = 152
 HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes (read + write) per frame of k_decode<double> on the 2 dB
+# workload with the library defaults, from one ncu capture of this build:
+# 1,034,160,896 read + 9,709,638,400 written over a 456-frame launch of
+# pool frames 0-455 (dram__bytes_read.sum, dram__bytes_write.sum), scaled
+# to a launch by its frame count. Mostly the dense fallback's
+# matrices leaving L2. Valid only for that kernel build and configuration.
+DRAM_BYTES_PER_FRAME_2DB = (1034160896 + 9709638400) / 456
 
 
 def measured_hbm_gbs():
@@ -403,9 +410,15 @@ def run_ours(args):
     sm_mhz = clocks["sm_mhz"] if clocks else 2070.0
     hbm_peak, hbm_src = measured_hbm_gbs()
     achieved = nbytes / t_total / 1e9
+    traffic = args.traffic_bytes
+    defaults = (args.ebn0 == 2.0 and args.precision == "fp64" and args.smem_budget == 0
+                and args.threads == 128 and args.precond == "column" and not args.warm_start
+                and not args.mts_reuse and args.dense_switch < 0)
+    if traffic is None and defaults:
+        traffic = DRAM_BYTES_PER_FRAME_2DB * B_   # per launch (one launch per step)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak,
-                "traffic": args.traffic_bytes,
+                "traffic": traffic,
                 "kernel": "k_decode (persistent, one CTA per frame)",
                 "peak_source": f"{hbm_src} HBM copy bandwidth",
                 "bytes": "algorithmic bytes of every PCG iteration (Q h index passes at 4 B, "
