@@ -249,9 +249,8 @@ k_pcg(CodeView C0, DevParams P, Layout L, const double* gamma, const uint8_t* in
         __syncthreads();
         bool force64 = false;
         bool force_dense = false;
-        int factor = 0;
         NewtonOut no = newton_solve<T>(B, C, W, F, Lv, P, P.tol_pcg, P.max_pcg, force64,
-                                       force_dense, factor);
+                                       force_dense);
         for (int r = B.tid; r < C.m; r += B.nt) dy[(size_t)f * C.m + r] = r < F.p ? W.dy[r] : 0.0;
         if (B.tid == 0) iters[f] = no.iters;
         __syncthreads();

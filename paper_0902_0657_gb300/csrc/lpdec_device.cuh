@@ -1820,59 +1820,6 @@ __device__ __forceinline__ bool chol_diag_block(double* A, int p, int k0, int kb
     return bad;
 }
 
-// Solves L L' x = b with the factor of dense_newton (column-major, leading
-// dimension p): y (holding b) := L^-1 y in place, then x := L'^-1 y, panel
-// by panel (one warp solves each 32 x 32 diagonal block, then every thread
-// updates its rows). y and x are distinct p-vectors.
-__device__ inline void chol_solve(Blk& B, const double* A, int p, double* y, double* x) {
-    const bool sweeper = B.warp == B.sw;
-    for (int k0 = 0; k0 < p; k0 += kDB) {
-        const int kb = min(kDB, p - k0);
-        if (sweeper)
-            for (int j = k0; j < k0 + kb; ++j) {
-                const double* cj = A + (size_t)j * p;
-                const double yj = y[j] / cj[j];
-                __syncwarp();
-                const int i = j + 1 + B.lane;
-                if (i < k0 + kb) y[i] -= cj[i] * yj;
-                if (B.lane == 0) y[j] = yj;
-                __syncwarp();
-            }
-        __syncthreads();
-        for (int i = k0 + kb + B.tid; i < p; i += B.nt) {
-            double v = y[i];
-            for (int t = 0; t < kb; ++t) v -= A[(size_t)(k0 + t) * p + i] * y[k0 + t];
-            y[i] = v;
-        }
-        __syncthreads();
-    }
-    for (int r = B.tid; r < p; r += B.nt) x[r] = y[r];
-    __syncthreads();
-    for (int k0 = ((p - 1) / kDB) * kDB; k0 >= 0; k0 -= kDB) {
-        const int kb = min(kDB, p - k0);
-        if (sweeper)
-            for (int j = k0 + kb - 1; j >= k0; --j) {
-                const double* cj = A + (size_t)j * p;
-                // x_j = (y_j - sum_{j < i < k0+kb} L(i,j) x_i) / L(j,j)
-                const int i = j + 1 + B.lane;
-                double part = i < k0 + kb ? cj[i] * x[i] : 0.0;
-                const double sum = warp_sum(part);
-                __syncwarp();
-                if (B.lane == 0) x[j] = (x[j] - sum) / cj[j];
-                __syncwarp();
-            }
-        __syncthreads();
-        // rows above the panel: x_i -= sum_t L(k0+t, i) x_{k0+t}
-        for (int i = B.tid; i < k0; i += B.nt) {
-            const double* ci = A + (size_t)i * p + k0;
-            double v = x[i];
-            for (int t = 0; t < kb; ++t) v -= ci[t] * x[k0 + t];
-            x[i] = v;
-        }
-        __syncthreads();
-    }
-}
-
 template <typename T>
 __device__ __noinline__ bool dense_newton(Blk& B, const CodeView C, WS<T> W, const Frame& F) {
     const int n = C.n, p = F.p;
@@ -1969,82 +1916,62 @@ __device__ __noinline__ bool dense_newton(Blk& B, const CodeView C, WS<T> W, con
         }
         __syncthreads();
     }
-    // L L' dy = w
+    // L y = w (into r64), panel by panel
     for (int r = B.tid; r < p; r += B.nt) W.r64[r] = W.w[r];
     __syncthreads();
-    chol_solve(B, A, p, W.r64, W.dy);
+    for (int k0 = 0; k0 < p; k0 += kDB) {
+        const int kb = min(kDB, p - k0);
+        if (sweeper)
+            for (int j = k0; j < k0 + kb; ++j) {
+                const double* cj = A + (size_t)j * p;
+                const double yj = W.r64[j] / cj[j];
+                __syncwarp();
+                const int i = j + 1 + B.lane;
+                if (i < k0 + kb) W.r64[i] -= cj[i] * yj;
+                if (B.lane == 0) W.r64[j] = yj;
+                __syncwarp();
+            }
+        __syncthreads();
+        for (int i = k0 + kb + B.tid; i < p; i += B.nt) {
+            double v = W.r64[i];
+            for (int t = 0; t < kb; ++t) v -= A[(size_t)(k0 + t) * p + i] * W.r64[k0 + t];
+            W.r64[i] = v;
+        }
+        __syncthreads();
+    }
+    // L' dy = y, panel by panel from the last
+    for (int r = B.tid; r < p; r += B.nt) W.dy[r] = W.r64[r];
+    __syncthreads();
+    for (int k0 = ((p - 1) / kDB) * kDB; k0 >= 0; k0 -= kDB) {
+        const int kb = min(kDB, p - k0);
+        if (sweeper)
+            for (int j = k0 + kb - 1; j >= k0; --j) {
+                const double* cj = A + (size_t)j * p;
+                // dy_j = (y_j - sum_{j < i < k0+kb} L(i,j) dy_i) / L(j,j)
+                const int i = j + 1 + B.lane;
+                double part = i < k0 + kb ? cj[i] * W.dy[i] : 0.0;
+                const double sum = warp_sum(part);
+                __syncwarp();
+                if (B.lane == 0) W.dy[j] = (W.dy[j] - sum) / cj[j];
+                __syncwarp();
+            }
+        __syncthreads();
+        // rows above the panel: dy_i -= sum_t L(k0+t, i) dy_{k0+t}
+        for (int i = B.tid; i < k0; i += B.nt) {
+            const double* ci = A + (size_t)i * p + k0;
+            double v = W.dy[i];
+            for (int t = 0; t < kb; ++t) v -= ci[t] * W.dy[k0 + t];
+            W.dy[i] = v;
+        }
+        __syncthreads();
+    }
     return true;
 }
-
-// PCG in FP64 on (A D^2 A') dy = w preconditioned by the dense Cholesky
-// factor an earlier Newton system of the same LP left in W.qd (Q changes
-// little from one interior-point iteration to the next, so the old factor
-// is a close preconditioner and a refactorization, p^3/6 FMAs, can often be
-// skipped). x0 = 0; stops at ||r|| < tol ||w|| (recurrence residual) or
-// after max_it iterations. Vectors: r in r64, z in vr1, h in vr2, l in v1,
-// the solve's scratch in v2, Q h's column pass in t64; dy out.
-template <typename T>
-__device__ inline int pcg_dense(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
-                                double tol, int max_it, double* relres) {
-    const int n = C.n, p = F.p;
-    double* r = W.r64;
-    double* z = W.vr1;
-    double* h = W.vr2;
-    double* l = W.v1;
-    double* y = W.v2;
-    for (int k = B.tid; k < p; k += B.nt) { W.dy[k] = 0.0; r[k] = W.w[k]; y[k] = W.w[k]; }
-    __syncthreads();
-    chol_solve(B, W.qd, p, y, z);
-    double zr0 = 0.0, rr0 = 0.0;
-    for (int k = B.tid; k < p; k += B.nt) { h[k] = z[k]; zr0 += z[k] * r[k]; rr0 += r[k] * r[k]; }
-    double2 s2 = bsum2(B, zr0, rr0);
-    double zr = s2.x, rr = s2.y;
-    const double rn0 = sqrt(rr);
-    *relres = 0.0;
-    if (rn0 == 0.0) return 0;
-    int it = 0;
-    while (sqrt(rr) >= tol * rn0 && it < max_it) {
-        for (int i = B.tid; i < n; i += B.nt) W.t64[i] = W.d2[i] * colA_T<double>(C, W, i, h);
-        __syncthreads();
-        double hl = 0.0;
-        for (int k = B.tid; k < p; k += B.nt) {
-            const double v = rowA<double>(C, W, k, W.t64) + W.d2[n + k] * h[k];
-            l[k] = v;
-            hl += h[k] * v;
-        }
-        hl = bsum(B, hl);
-        if (!(hl > 0.0) || !isfinite(hl)) break;
-        const double alpha = zr / hl;
-        for (int k = B.tid; k < p; k += B.nt) {
-            W.dy[k] += alpha * h[k];
-            const double v = r[k] - alpha * l[k];
-            r[k] = v;
-            y[k] = v;
-        }
-        __syncthreads();
-        chol_solve(B, W.qd, p, y, z);
-        double zr_l = 0.0, rr_l = 0.0;
-        for (int k = B.tid; k < p; k += B.nt) { zr_l += z[k] * r[k]; rr_l += r[k] * r[k]; }
-        s2 = bsum2(B, zr_l, rr_l);
-        const double nu = s2.x / zr;
-        zr = s2.x;
-        rr = s2.y;
-        for (int k = B.tid; k < p; k += B.nt) h[k] = z[k] + nu * h[k];
-        __syncthreads();
-        ++it;
-    }
-    *relres = isfinite(rr) ? sqrt(rr) / rn0 : INFINITY;
-    return it;
-}
-
-// PCG iterations tried on an LP's previous dense factor before refactoring.
-constexpr int kFactorReuseIters = 16;
 
 template <typename T>
 __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                          const Levels& L, const DevParams& P, double tol,
-                                         int max_it, bool& force64, bool& force_dense,
-                                         int& factor) {
+                                         int max_it, bool& force64, bool& force_dense) {
     const int p = F.p;
     double ww = 0.0;
     for (int r = B.tid; r < p; r += B.nt) { W.dy[r] = 0.0; W.r64[r] = W.w[r]; ww += W.w[r] * W.w[r]; }
@@ -2055,32 +1982,14 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
     const int nnz_m = p + (int)W.bptr[p];
     double rn = wn;
     const bool dense_ok = W.qd != nullptr && F.p <= W.dense_p;
-    // factor: 0 = W.qd holds no factor of this LP, 1 = it holds the factor
-    // of an earlier Newton system (tried first; a failure costs at most
-    // kFactorReuseIters PCG iterations, a small part of a refactorization)
-    if (force_dense && dense_ok && factor == 1) {
-        double rel;
-        const int it = pcg_dense<T>(B, C, W, F, tol, kFactorReuseIters, &rel);
-        double rr;
-        residual64<double, T>(B, C, W, F, &rr);
-        o.iters += it;
-        o.iters64 += it;
-        o.flops += it * (4.0 * F.ea + 2.0 * (double)F.p * F.p + C.n + 10.0 * F.p);
-        if (sqrt(rr) < tol * wn) {
-            o.relres = sqrt(rr) / wn;
-            return o;
-        }
-    }
     if (force_dense && dense_ok && dense_newton<T>(B, C, W, F)) {   // PCG already failed in this LP
         double rr;
         residual64<double, T>(B, C, W, F, &rr);
         o.dense = 1;
         o.relres = sqrt(rr) / wn;
         o.flops += dense_flops(F, C.n);
-        factor = 1;
         return o;
     }
-    if (force_dense && dense_ok) factor = 0;   // (the failed factorization left no factor)
     bool use64 = sizeof(T) == 8 || force64;
     // LPDEC_M32: FP32 M-solves until one round stalls, then FP64 M-solves
     // for the rest of this LP (force64 is sticky across its Newton solves)
@@ -2148,9 +2057,6 @@ __device__ inline NewtonOut newton_solve(Blk& B, const CodeView& C, WS<T>& W, co
             o.dense = 1;
             o.relres = sqrt(rr) / wn;
             o.flops += dense_flops(F, C.n);
-            factor = 1;
-        } else {
-            factor = 0;
         }
     }
     return o;
@@ -2192,11 +2098,9 @@ __device__ __forceinline__ double cost_of(const double* gamma, int n, int i) {
     return i < n ? fabs(gamma[i]) : 0.0;
 }
 
-// it_cap bounds the CG iterations of a speculative attempt (0: the basis
-// size bound alone).
 template <typename T>
 __device__ __noinline__ int certify(Blk& B, const CodeView C, WS<T> W, const Frame& F,
-                              const double* gamma, int it_cap = 0) {
+                              const double* gamma) {
     const int n = C.n, p = F.p, q = F.q;
     double nbasic = 0.0, cmax = 0.0;
     for (int i = B.tid; i < q; i += B.nt) {
@@ -2209,8 +2113,7 @@ __device__ __noinline__ int certify(Blk& B, const CodeView C, WS<T> W, const Fra
     }
     double2 nb = bsum2(B, nbasic, 0.0);
     cmax = -bmin2(B, -cmax, 0.0).x;
-    int max_it = 2 * (int)nb.x + 50;   // CG on the basis: at most its size in exact arithmetic
-    if (it_cap > 0) max_it = min(max_it, it_cap);
+    const int max_it = 2 * (int)nb.x + 50;   // CG on the basis: at most its size in exact arithmetic
     // --- primal: CGLS on A_B d = s, s = b - A_B x_B
     double* d = W.v1; double* g = W.v2; double* h = W.v3; double* sr = W.vr1; double* lr = W.vr2;
     double ss = 0.0, bb = 0.0;
@@ -2380,8 +2283,6 @@ __device__ __noinline__ int certify_basis(Blk& B, const CodeView C, WS<T> W, con
 constexpr int kTrace = 10;
 // Least x_i, z_i of a warm start (lpdec_params.warm_start).
 constexpr double kWarmFloor = 1e-2;
-// CG iterations of a speculative certificate inside the interior-point loop.
-constexpr int kSpecCertIters = 256;
 
 struct IpmOut {
     int iters, pcg_iters, pcg_iters64, converged, certified, max_levels, dense;
@@ -2427,7 +2328,6 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Fram
     }
     F.normc = sqrt(bsum(B, nc2));   // (barrier inside)
     bool force64 = false, force_dense = false;
-    int factor = 0;   // state of the LP's dense factor in W.qd (newton_solve)
     int last_pcg = 0;
     // preconditioner of this LP's Newton systems (LPDEC_MTS_ADAPTIVE starts
     // column-wise and turns incremental for good after a long PCG run)
@@ -2450,9 +2350,8 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Fram
                 if (W.x[i] > W.zz[i]) { c0 += 1.0; c1 += (double)(i + 1) * (double)(i + 1); }
             double2 sg = bsum2(B, c0, c1);
             if (sg.x == sig0 && sg.y == sig1) {
-                // (speculative: CG capped; the LP's final certificate is not)
                 const unsigned long long tc = global_ns();
-                const int okc = certify<T>(B, C, W, F, gamma, kSpecCertIters);
+                const int okc = certify<T>(B, C, W, F, gamma);
                 o.t_cert += since(tc);
                 if (okc) {
                     o.converged = 1;
@@ -2538,8 +2437,7 @@ __device__ __noinline__ IpmOut ipm_solve(Blk& B, const CodeView C, WS<T> W, Fram
         if (W.lz && B.tid == 0) { W.lz[2 * kLz] = 0.0; W.lz[2 * kLz + 1] = 0.0; }
         __syncthreads();
         tp = global_ns();
-        NewtonOut no = newton_solve<T>(B, C, W, F, L, P, tol, P.max_pcg, force64, force_dense,
-                                       factor);
+        NewtonOut no = newton_solve<T>(B, C, W, F, L, P, tol, P.max_pcg, force64, force_dense);
         if (no.dense) o.t_dense += since(tp);
         else o.t_pcg += since(tp);
         o.dense += no.dense;
