@@ -503,12 +503,13 @@ Layout make_layout(const Dims& d, size_t budget, size_t real_bytes, bool m32, in
         {S_CUR, I * (P + 2), 1},
         // budgeted arrays in priority order: first what every PCG iteration
         // reads on its serial path (the two level-scheduled triangular
-        // solves: values, dependency lists and ranges, level rows, pivot
-        // signs), then what the serial greedy of the MTS selection walks
-        // once per interior-point iteration (pivots, degrees, levels, the
-        // column and row entries of A), then the rest of the sparse passes
-        // and the level build, then the cut search and the cut list, and
-        // last the vectors of the parallel passes of Q h (and sort keys)
+        // solves: right side, solution and pivot scaling, dependency lists
+        // and ranges, level rows, pivot signs), then what the serial greedy
+        // of the MTS selection walks once per interior-point iteration
+        // (pivots, degrees, levels, the column and row entries of A), then
+        // the rest of the level build, then the cut search and the cut
+        // list, and last the vectors only the parallel passes touch (and
+        // the sort keys)
         {S_VEC, vec, 0}, {S_BDEP, H * ea, 0}, {S_FDEP, H * ea, 0}, {S_LBSE, 8 * P, 0},
         {S_LFSE, 8 * P, 0}, {S_LBROWS, H * P, 0}, {S_LFROWS, H * P, 0}, {S_PSGN, P, 0},
         {S_PIVCOL, H * P, 0}, {S_PIVROW, H * q, 0}, {S_LF, H * P, 0}, {S_LB, H * P, 0},

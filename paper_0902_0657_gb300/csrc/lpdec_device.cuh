@@ -77,11 +77,11 @@ enum Arr {
     S_BPTR, S_BDEP, S_FPTR, S_FDEP,   // dependency lists of the two triangular solves
     S_LBSE, S_LFSE,   // per level position: the dependency range of its row (sweep order)
     S_VEC,      // PCG vectors the triangular sweeps read on their serial path, type T:
-                // xs, r, z, h, l, invd2p (pmax each) [+ 3 FP32 vectors, LPDEC_M32];
-                // during the MTS selection the same bytes hold rank [q] and sorted [q]
-    S_VECC,     // PCG vectors of the parallel passes of Q h, type T: t (n), d2t (n+pmax);
-                // during the MTS selection the same bytes hold the sort keys (u64 [q2],
-                // u32 [q2])
+                // r, z, invd2p (pmax each) [+ 3 FP32 vectors, LPDEC_M32]; during the
+                // MTS selection the same bytes hold rank [q] and sorted [q]
+    S_VECC,     // PCG vectors only the parallel passes touch, type T: xs, h, l (pmax
+                // each), t (n), d2t (n+pmax); during the MTS selection the same bytes
+                // hold the sort keys (u64 [q2], u32 [q2])
     // FP64 interior-point state (global scratch)
     G_X, G_Z, G_RC, G_D2, G_Y, G_B, G_W, G_DY, G_R64, G_U, G_T64, G_BASIC,
     // optimality certificate scratch: vertex and CG vectors over columns
@@ -113,20 +113,22 @@ constexpr uint32_t kGlobalBit = 0x80000000u;
 __host__ __device__ constexpr size_t vec_elems(int n, int pmax) {
     return 7 * (size_t)pmax + 2 * (size_t)n;
 }
-// Bytes of the S_VEC block: xs, r, z, h, l, invd2p in type T and, for
-// LPDEC_M32, three FP32 vectors after them (the M-solve's right side and
-// solution, and 1/d^2 of the pivot columns); at least rank and sorted.
+// Bytes of the S_VEC block: r, z, invd2p in type T and, for LPDEC_M32,
+// three FP32 vectors after them (the M-solve's right side and solution, and
+// 1/d^2 of the pivot columns); at least rank and sorted.
 __host__ __device__ constexpr size_t vec_hot_bytes(int n, int pmax, size_t real_bytes, bool m32) {
-    return (real_bytes * 6 * (size_t)pmax + (m32 ? 12 * (size_t)pmax : 0)) >
+    return (real_bytes * 3 * (size_t)pmax + (m32 ? 12 * (size_t)pmax : 0)) >
                    4 * ((size_t)n + pmax)
-               ? real_bytes * 6 * (size_t)pmax + (m32 ? 12 * (size_t)pmax : 0)
+               ? real_bytes * 3 * (size_t)pmax + (m32 ? 12 * (size_t)pmax : 0)
                : 4 * ((size_t)n + pmax);
 }
-// Bytes of the S_VECC block: t, d2t in type T, at least the sort keys.
+// Bytes of the S_VECC block: xs, h, l, t, d2t in type T, at least the sort
+// keys.
 __host__ __device__ constexpr size_t vec_cold_bytes(int n, int pmax, size_t real_bytes,
                                                     size_t q2) {
-    return real_bytes * (2 * (size_t)n + pmax) > 12 * q2 ? real_bytes * (2 * (size_t)n + pmax)
-                                                         : 12 * q2;
+    return real_bytes * (2 * (size_t)n + 4 * (size_t)pmax) > 12 * q2
+               ? real_bytes * (2 * (size_t)n + 4 * (size_t)pmax)
+               : 12 * q2;
 }
 
 struct Layout {
@@ -211,12 +213,12 @@ __device__ inline void point_ws(WS<T>& w, const Layout& L, char* smem, char* gws
         T* v = reinterpret_cast<T*>(ws_ptr(L, S_VEC, smem, gws));
         w.rank = reinterpret_cast<uint16_t*>(v);
         w.sorted = w.rank + (n + pm);
-        w.xs = v; v += pm; w.r = v; v += pm; w.z = v; v += pm; w.h = v; v += pm; w.l = v; v += pm;
-        w.invd2p = v;
+        w.r = v; v += pm; w.z = v; v += pm; w.invd2p = v;
         w.rf = reinterpret_cast<float*>(w.invd2p + pm); w.zf = w.rf + pm; w.ip32 = w.zf + pm;
         T* c = reinterpret_cast<T*>(ws_ptr(L, S_VECC, smem, gws));
         w.skey = reinterpret_cast<unsigned long long*>(c);
         w.sidx = reinterpret_cast<uint32_t*>(w.skey + L.q2);
+        w.xs = c; c += pm; w.h = c; c += pm; w.l = c; c += pm;
         w.t = c; c += n; w.d2t = c;
     }
     P_(double, x, G_X); P_(double, zz, G_Z); P_(double, rc, G_RC); P_(double, d2, G_D2);
