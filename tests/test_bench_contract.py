@@ -38,3 +38,17 @@ def test_binding_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(L, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         L.lpdec_default_params()
+
+
+def test_serving_latency_summary_counts_unserved_frames_as_slowest():
+    """Serving latencies: frames still running at a level's end (NaN) rank
+    above every served frame; a percentile that falls on them is None."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    lat = np.array([0.1] * 98 + [np.nan, np.nan])   # 98 served in 100 ms, 2 cut off
+    s = bench.latency_summary(lat, 100)
+    assert s["p50_ms"] == pytest.approx(100.0) and s["max_served_ms"] == pytest.approx(100.0)
+    assert s["p99_ms"] is None and s["p99.9_ms"] is None
+    s = bench.latency_summary(np.linspace(0.001, 1.0, 1000), 1000)
+    assert s["p50_ms"] == pytest.approx(501.0, rel=1e-3) and s["p99.9_ms"] == pytest.approx(1000.0)
