@@ -120,6 +120,11 @@ extern "C" {
  *                     is redone by a dense FP64 Cholesky factorization of
  *                     A D^2 A' (LPs of up to 2048 rows), and so are the
  *                     remaining Newton solves of that LP
+ *   dense_switch = 64 a Newton solve whose PCG converges only after more
+ *                     than 64 max(1, (p/512)^2) iterations also sends the
+ *                     rest of its LP to the dense solve (cheaper there)
+ *   order_frames = 1  frames of a one-code batch with more frames than CTAs
+ *                     are handed out hardest first (results unchanged)
  *   variant = LPDEC_MALP_A, precision = LPDEC_FP64
  *   precond = LPDEC_MTS_COLUMN, precond_switch = 150, warm_start = 0,
  *   mts_reuse = 0 (the paper's future work, Sections V and VII: the
