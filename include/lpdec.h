@@ -29,6 +29,10 @@
  *     device, owned by the caller; *_device entry points are asynchronous
  *     on the given stream (a cudaStream_t passed as void*, NULL = legacy
  *     default stream) and the caller synchronises.
+ *   - A context's device scratch (per-CTA workspaces, the frame queue
+ *     counter, the frame-order keys) serves one batch at a time: calls on
+ *     one context must run in order on the GPU (one stream, or synchronised
+ *     between streams); decode concurrently with one context per stream.
  *   - Frame-major layout: array "[nframes x n]" holds frame f at offset f*n.
  *   - Cut masks: for check j, bit e of mask[j] is set iff the e-th
  *     neighbour of j (in the CSR column order of row j) belongs to the odd
