@@ -121,29 +121,40 @@ def incremental(A, w):
 # Algorithm 8: row-wise greedy search with diagonal expansion
 # ---------------------------------------------------------------------------
 
-def rowwise(A, w, n):
+def rowwise(A, w, n, expansion="diagonal"):
     """Algorithm 8: peel degree-1 rows (lowest index first); when none is
-    left, zero the minimum-weight nonzero column. Rows never peeled are then
-    paired with their own slack columns n + j (diagonal expansion)."""
+    left, zero the minimum-weight nonzero column (ties: lowest index).
+
+    expansion = "diagonal" (Algorithm 8 as printed): rows never peeled are
+    then paired with their own slack columns n + j, in increasing j.
+    expansion = "triangular" (Section V-A's alternative): the same search is
+    run again on the columns of A that have no nonzero in any row peeled so
+    far (so the new pivots extend the lower-triangular set), and again,
+    until every row is peeled; each such round peels at least one row,
+    because every row not yet peeled keeps its own slack column."""
     A = np.asarray(A) != 0
     p, q = A.shape
-    alive_c = A.any(axis=0)
     used_r = np.zeros(p, dtype=bool)
     col, row = [], []
-    while alive_c.any():
-        deg = (A[:, alive_c]).sum(axis=1)
-        cand = np.flatnonzero(deg == 1)
-        if cand.size:
-            j = int(cand[0])
-            i = int(np.flatnonzero(A[j] & alive_c)[0])
-            col.append(i)
-            row.append(j)
-            used_r[j] = True
-            alive_c[i] = False
-        else:
-            live = np.flatnonzero(alive_c)
-            i = int(min(live, key=lambda t: (float(w[t]), t)))
-            alive_c[i] = False
+    alive_c = A.any(axis=0)
+    while True:
+        while alive_c.any():
+            deg = (A[:, alive_c]).sum(axis=1)
+            cand = np.flatnonzero(deg == 1)
+            if cand.size:
+                j = int(cand[0])
+                i = int(np.flatnonzero(A[j] & alive_c)[0])
+                col.append(i)
+                row.append(j)
+                used_r[j] = True
+                alive_c[i] = False
+            else:
+                live = np.flatnonzero(alive_c)
+                i = int(min(live, key=lambda t: (float(w[t]), t)))
+                alive_c[i] = False
+        if expansion != "triangular" or used_r.all():
+            break
+        alive_c = A.any(axis=0) & ~A[used_r].any(axis=0)
     for j in range(p):
         if not used_r[j]:
             col.append(n + j)

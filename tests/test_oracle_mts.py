@@ -96,6 +96,50 @@ def test_triangulation_and_rowwise_structure():
         assert tri is not None
 
 
+def test_rowwise_triangular_expansion_by_hand():
+    """Section V-A's triangular expansion on a 2-row LP worked by hand:
+    rows r0 = {c0, c1, s0}, r1 = {c0, c1, c2, s1}, weights c0 5, c1 0.3,
+    c2 0.25, s0 0.1, s1 0.2. The search zeroes s0, s1, c2, c1 (least weight
+    first, no row of degree one before), then r0 and r1 both hold only c0:
+    r0 peels it and r1 is left empty. The diagonal expansion gives r1 its
+    slack s1; the triangular expansion searches the columns without a
+    nonzero in r0, {c2, s1}: it zeroes s1 (the lighter) and r1 peels c2."""
+    A = np.array([[1, 1, 0, 1, 0], [1, 1, 1, 0, 1]])
+    w = np.array([5.0, 0.3, 0.25, 0.1, 0.2])
+    col, row = mts.rowwise(A, w, 3)
+    assert list(col) == [0, 4] and list(row) == [0, 1]
+    col, row = mts.rowwise(A, w, 3, "triangular")
+    assert list(col) == [0, 2] and list(row) == [0, 1]
+
+
+def test_rowwise_triangular_expansion_structure():
+    """On LPs of decodes: the triangular expansion gives a full lower-
+    triangular set with unit diagonal; it starts with the same pivots as
+    the diagonal expansion (the first search is the same), keeps every
+    column of a later round free of the rows peeled before it, and never
+    needs more slack columns than the diagonal expansion adds."""
+    rng = np.random.default_rng(9)
+    differs = 0
+    for code, g, L, _ in lps_of_frames()[:8]:
+        p, q = L.A.shape
+        for w in (rng.random(q), np.exp(rng.normal(size=q) * 4)):
+            cd, rd = mts.rowwise(L.A, w, code.n)
+            ct, rt = mts.rowwise(L.A, w, code.n, "triangular")
+            assert len(ct) == p and sorted(rt) == list(range(p)) and len(set(ct)) == p
+            T = L.A[np.ix_(rt, ct)]
+            assert np.allclose(np.triu(T, 1), 0) and np.all(np.abs(np.diag(T)) == 1)
+            # pivots of the first search: the diagonal result up to its tail of
+            # slack columns in increasing rows (the expansion)
+            k1 = 0
+            while k1 < p and not (cd[k1] >= code.n and list(rd[k1:]) == sorted(rd[k1:])
+                                  and all(cd[k1:] == code.n + rd[k1:])):
+                k1 += 1
+            assert list(ct[:k1]) == list(cd[:k1]) and list(rt[:k1]) == list(rd[:k1])
+            assert np.sum(ct >= code.n) <= np.sum(cd >= code.n)
+            differs += not np.array_equal(ct, cd)
+    assert differs > 0
+
+
 def test_lemma2_and_theorem5_on_integral_lps():
     """Lemma 2: the basic set of an integral LP has no stopping set
     (Algorithm 5 triangulates it). Theorem 5: near the optimum, the
