@@ -76,7 +76,8 @@ def parse_args():
                     help="fp64: FP64 PCG; mixed: FP32 PCG refined in FP64; "
                          "m32: FP64 PCG with an FP32 preconditioner solve")
     ap.add_argument("--threads", type=int, default=128)
-    ap.add_argument("--precond", choices=["column", "incremental", "rowwise", "adaptive"],
+    ap.add_argument("--precond", choices=["column", "incremental", "rowwise", "adaptive",
+                                          "rowwise-tri"],
                     default="column", help="triangular-set preconditioner (Section V)")
     ap.add_argument("--warm-start", type=int, default=0,
                     help="1: interior-point warm start across the LPs of a frame")
@@ -274,7 +275,8 @@ def run_ours(args):
     prm.threads_per_block = args.threads
     prm.smem_budget = args.smem_budget
     prm.precond = {"column": L.LPDEC_MTS_COLUMN, "incremental": L.LPDEC_MTS_INCREMENTAL,
-                   "rowwise": L.LPDEC_MTS_ROWWISE, "adaptive": L.LPDEC_MTS_ADAPTIVE}[args.precond]
+                   "rowwise": L.LPDEC_MTS_ROWWISE, "adaptive": L.LPDEC_MTS_ADAPTIVE,
+                   "rowwise-tri": L.LPDEC_MTS_ROWWISE_TRI}[args.precond]
     prm.warm_start = args.warm_start
     prm.mts_reuse = args.mts_reuse
     prm.order_frames = args.order
@@ -711,7 +713,8 @@ def run_c3(args):
         if args.max_pcg > 0:
             prm.max_pcg = args.max_pcg
         prm.precond = {"column": L.LPDEC_MTS_COLUMN, "incremental": L.LPDEC_MTS_INCREMENTAL,
-                       "rowwise": L.LPDEC_MTS_ROWWISE, "adaptive": L.LPDEC_MTS_ADAPTIVE}[args.precond]
+                       "rowwise": L.LPDEC_MTS_ROWWISE, "adaptive": L.LPDEC_MTS_ADAPTIVE,
+                   "rowwise-tri": L.LPDEC_MTS_ROWWISE_TRI}[args.precond]
         with L.Decoder(code, params=prm) as d:
             d_g = torch.from_numpy(G).cuda()
             d_u = torch.empty((nf, code.n), dtype=torch.float64, device="cuda")

@@ -77,6 +77,10 @@ extern "C" {
 #define LPDEC_MTS_ADAPTIVE    3   /* column-wise; an LP switches to the incremental search
                                      for its remaining Newton systems once one needed more
                                      than precond_switch PCG iterations */
+#define LPDEC_MTS_ROWWISE_TRI 4   /* the row-wise greedy search with the triangular
+                                     expansion of Section V-A: the search is run again
+                                     on the columns free of the rows peeled so far,
+                                     until every row is peeled */
 
 /* Arithmetic of the PCG solve (the IPM state is always FP64). */
 #define LPDEC_FP64  0   /* FP64 PCG */

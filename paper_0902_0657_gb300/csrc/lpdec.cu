@@ -722,7 +722,7 @@ bool params_ok(const lpdec_params& p) {
         return false;
     if (p.precision != LPDEC_FP64 && p.precision != LPDEC_MIXED && p.precision != LPDEC_M32)
         return false;
-    if (p.precond < LPDEC_MTS_COLUMN || p.precond > LPDEC_MTS_ADAPTIVE) return false;
+    if (p.precond < LPDEC_MTS_COLUMN || p.precond > LPDEC_MTS_ROWWISE_TRI) return false;
     if (p.lane_policy != 0 && p.lane_policy != 1 && p.lane_policy != 2 && p.lane_policy != 4 &&
         p.lane_policy != 8)
         return false;

@@ -928,7 +928,7 @@ __device__ __forceinline__ void bit_clear(uint32_t* bm, int i) { atomicAnd(&bm[i
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __noinline__ Levels mts_rowwise(Blk& B, const CodeView C, WS<T> W, const Frame& F,
-                                     const double* wt) {
+                                     const double* wt, bool tri) {
     const int n = C.n, p = F.p, q = F.q;
     uint16_t* rowdeg = W.lb;
     for (int i = B.tid; i < q; i += B.nt) {
@@ -948,7 +948,8 @@ __device__ __noinline__ Levels mts_rowwise(Blk& B, const CodeView C, WS<T> W, co
         int live = 0;
         for (int i = lane; i < q; i += 32) live += W.deg[i];
         for (int o = 16; o > 0; o >>= 1) live += __shfl_xor_sync(kFull, live, o);
-        int k = 0, lo = q - 1;
+        int k = 0, lo = q - 1, k_round = -1;
+        for (;;) {   // one search (Algorithm 8), then rounds of the triangular expansion
         while (live > 0) {
             const unsigned j = warp_first_bit(W.bitmap, nwr, lane);
             int victim;
@@ -992,7 +993,39 @@ __device__ __noinline__ Levels mts_rowwise(Blk& B, const CodeView C, WS<T> W, co
             --live;
             __syncwarp();
         }
-        // diagonal expansion
+        // triangular expansion (Section V-A): the same search again over the
+        // columns with no nonzero in a row peeled so far, until every row is
+        // peeled (each round peels one at least: every row left keeps its
+        // slack column)
+        if (!tri || k >= p || k == k_round) break;   // (a round without a peel ends it)
+        k_round = k;
+        int lv = 0;
+        for (int c = lane; c < q; c += 32) {
+            const int nr = col_nrows(W, n, c);
+            int ok = nr > 0 ? 1 : 0;
+            for (int t = 0; t < nr && ok; ++t)
+                if (W.pivcol[col_row(W, n, c, t)] != kNone) ok = 0;
+            W.deg[c] = (uint16_t)ok;
+            lv += ok;
+        }
+        for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(kFull, lv, o);
+        for (int wd = lane; wd < nwr; wd += 32) W.bitmap[wd] = 0;
+        __syncwarp();
+        for (int r = lane; r < p; r += 32) {
+            int d = 0;
+            if (W.pivcol[r] == kNone) {
+                for (uint32_t e = W.rptr[r]; e < W.rptr[r + 1]; ++e) d += W.deg[W.rowent[e] & kIdx];
+                d += W.deg[n + r];
+            }
+            rowdeg[r] = (uint16_t)d;
+            if (d == 1) bit_set(W.bitmap, r);
+        }
+        __syncwarp();
+        if (lv == 0) break;
+        live = lv;
+        lo = q - 1;
+        }
+        // diagonal expansion (rows never peeled)
         for (int base = 0; base < p; base += 32) {
             const int j = base + lane;
             const bool need = j < p && W.pivcol[j] == kNone;
@@ -1225,7 +1258,8 @@ template <typename T>
 __device__ inline Levels select_mts(Blk& B, const CodeView& C, WS<T>& W, const Frame& F,
                                     const double* wt, int kind) {
     if (kind == LPDEC_MTS_INCREMENTAL) return mts_incremental<T>(B, C, W, F, wt);
-    if (kind == LPDEC_MTS_ROWWISE) return mts_rowwise<T>(B, C, W, F, wt);
+    if (kind == LPDEC_MTS_ROWWISE || kind == LPDEC_MTS_ROWWISE_TRI)
+        return mts_rowwise<T>(B, C, W, F, wt, kind == LPDEC_MTS_ROWWISE_TRI);
     return mts_select<T>(B, C, W, F, wt, 0);
 }
 

@@ -32,6 +32,7 @@ LPDEC_MTS_COLUMN = 0
 LPDEC_MTS_INCREMENTAL = 1
 LPDEC_MTS_ROWWISE = 2
 LPDEC_MTS_ADAPTIVE = 3
+LPDEC_MTS_ROWWISE_TRI = 4
 LPDEC_FP64 = 0
 LPDEC_MIXED = 1
 LPDEC_M32 = 2

@@ -36,7 +36,7 @@ def compare_frame(res, u, hard, cert, masks, st, ctx=""):
     (L.LPDEC_M32, 128, L.LPDEC_MTS_COLUMN), (L.LPDEC_FP64, 32, L.LPDEC_MTS_COLUMN),
     (L.LPDEC_MIXED, 256, L.LPDEC_MTS_COLUMN), (L.LPDEC_M32, 64, L.LPDEC_MTS_COLUMN),
     (L.LPDEC_FP64, 128, L.LPDEC_MTS_INCREMENTAL), (L.LPDEC_FP64, 128, L.LPDEC_MTS_ROWWISE),
-    (L.LPDEC_FP64, 128, L.LPDEC_MTS_ADAPTIVE)])
+    (L.LPDEC_FP64, 128, L.LPDEC_MTS_ADAPTIVE), (L.LPDEC_FP64, 128, L.LPDEC_MTS_ROWWISE_TRI)])
 def test_decode_gallager120_200_frames(precision, threads, precond):
     """(3,6) n=120, Eb/N0 2.0 dB, 200 frames from seed 0, in FP64, in mixed
     precision (FP32 PCG refined against FP64 residuals) and with the FP32

@@ -71,10 +71,11 @@ def test_cut_search_bit_exact(dec120):
 
 
 @pytest.mark.parametrize("kind", [L.LPDEC_MTS_COLUMN, L.LPDEC_MTS_INCREMENTAL,
-                                  L.LPDEC_MTS_ROWWISE])
+                                  L.LPDEC_MTS_ROWWISE, L.LPDEC_MTS_ROWWISE_TRI])
 def test_mts_selection_bit_exact(kind):
     """Algorithms 7 (column-wise), 6 with 5 (incremental) and 8 (row-wise
-    with diagonal expansion): the selected (column, row) pairs in selection
+    with diagonal expansion, and with Section V-A's triangular expansion):
+    the selected (column, row) pairs in selection
     order equal the oracle's, on LPs of oracle decodes with random weights,
     quantised weights (ties) and weights that differ below single
     precision."""
@@ -107,14 +108,17 @@ def test_mts_selection_bit_exact(kind):
             ec, er = omts.colwise(lp.A, w)
         elif kind == L.LPDEC_MTS_INCREMENTAL:
             ec, er = omts.incremental(lp.A, w)
-        else:
+        elif kind == L.LPDEC_MTS_ROWWISE:
             ec, er = omts.rowwise(lp.A, w, code.n)
+        else:
+            ec, er = omts.rowwise(lp.A, w, code.n, "triangular")
         assert np.array_equal(col[f, :lp.p], ec), (kind, f)
         assert np.array_equal(row[f, :lp.p], er), (kind, f)
         assert np.all(col[f, lp.p:] == -1)
 
 
-@pytest.mark.parametrize("kind", [L.LPDEC_MTS_INCREMENTAL, L.LPDEC_MTS_ROWWISE])
+@pytest.mark.parametrize("kind", [L.LPDEC_MTS_INCREMENTAL, L.LPDEC_MTS_ROWWISE,
+                                  L.LPDEC_MTS_ROWWISE_TRI])
 def test_pcg_with_each_preconditioner_matches_dense_solve(kind):
     """PCG (Algorithm 4) preconditioned by the incremental and row-wise
     triangular sets (lower triangular: the level schedules run in the other
