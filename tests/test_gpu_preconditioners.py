@@ -1,6 +1,7 @@
 """The preconditioner study of Section VI-B and its spectral remarks, on the
 GPU through the C ABI (lpdec_pcg_trace_device): plain CG and PCG with the
-three triangular-set preconditioners (Algorithms 6, 7, 8) on Newton systems
+triangular-set preconditioners (Algorithms 6, 7, 8, and 8 with the
+triangular expansion of Section V-A) on Newton systems
 of late interior-point iterations of fractional LPs of a (3,6) n = 2000
 code at 1.5 and 1.0 dB (inputs from the oracle: tests/golden/
 precond_study_peg2000.json, written by tests/golden/make_precond_study.py).
@@ -40,7 +41,8 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "precond_study_peg2000.json")
 KINDS = [("CG", None), ("column (Alg. 7)", L.LPDEC_MTS_COLUMN),
-         ("incremental (Alg. 6)", L.LPDEC_MTS_INCREMENTAL), ("row-wise (Alg. 8)", L.LPDEC_MTS_ROWWISE)]
+         ("incremental (Alg. 6)", L.LPDEC_MTS_INCREMENTAL), ("row-wise (Alg. 8)", L.LPDEC_MTS_ROWWISE),
+         ("row-wise, triangular expansion", L.LPDEC_MTS_ROWWISE_TRI)]
 
 
 def traced(torch, code, kind, g, in_lp, mask, D2, Wv, tol, max_hist):
@@ -87,8 +89,10 @@ def test_traced_pcg_matches_oracle_pcg():
                 col, row = omts.colwise(lp.A, D2[f, :lp.q])
             elif kind == L.LPDEC_MTS_INCREMENTAL:
                 col, row = omts.incremental(lp.A, D2[f, :lp.q])
-            else:
+            elif kind == L.LPDEC_MTS_ROWWISE:
                 col, row = omts.rowwise(lp.A, D2[f, :lp.q], code.n)
+            else:
+                col, row = omts.rowwise(lp.A, D2[f, :lp.q], code.n, "triangular")
             res, coef = [], []
             x, it = omts.pcg(lp.A, D2[f, :lp.q], Wv[f, :lp.p], col, row, 1e-10, 400,
                              residuals=res, coefficients=coef)
