@@ -457,7 +457,7 @@ int32_t lpdec_lp_solve_trace_device(lpdec_ctx* ctx, const lpdec_code* code,
  *     GPU (other streams, other threads) race on the array: serialize them.
  *   - The dense Cholesky fallback of stalled Newton solves runs as in the
  *     regular entry whenever one CTA's workspace with its matrix fits the
- *     array (n = 1008: about 3.8 MB per CTA, so 8 CTAs run at once instead
+ *     array (n = 1008: about 3.9 MB per CTA, so 8 CTAs run at once instead
  *     of the regular entry's 456); only codes whose matrix alone outgrows the
  *     array run without it, and a frame whose PCG stalls there may end
  *     LPDEC_ERR_NOT_CONVERGED where the regular entry converges.
