@@ -373,10 +373,13 @@ int32_t lpdec_cut_search_device(lpdec_ctx* ctx, const lpdec_code* code,
                                 const uint8_t* d_active, uint8_t* d_in_lp,
                                 uint32_t* d_mask, int32_t* d_flag, void* stream);
 
-/* Column-wise greedy MTS (Algorithm 7) of the LP given by (gamma, in_lp,
- * mask) with column weights w[nframes x (n+m)] (the decoder uses
- * w_i = d_i^2 = x_i / z_i; ties go to the lower column index). Writes the
- * selection order: col[nframes x m] (column chosen at step k) and
+/* Maximum-weight triangular set of the LP given by (gamma, in_lp, mask)
+ * with column weights w[nframes x (n+m)] (the decoder uses w_i = d_i^2 =
+ * x_i / z_i; ties go to the lower column index), by the context's
+ * lpdec_params.precond: column-wise (Algorithm 7, also for
+ * LPDEC_MTS_ADAPTIVE), incremental (Algorithm 6 with 5), row-wise with the
+ * diagonal (Algorithm 8) or the triangular expansion (Section V-A). Writes
+ * the selection order: col[nframes x m] (column chosen at step k) and
  * row[nframes x m] (its LP row); entries k >= p are -1. */
 int32_t lpdec_mts_select_device(lpdec_ctx* ctx, const lpdec_code* code,
                                 int32_t nframes, const double* d_gamma,
