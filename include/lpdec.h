@@ -387,10 +387,12 @@ int32_t lpdec_mts_select_device(lpdec_ctx* ctx, const lpdec_code* code,
                                 const double* d_w, int32_t* d_col, int32_t* d_row,
                                 void* stream);
 
-/* PCG (Algorithm 4) with the Algorithm 7 preconditioner (weights d2) for
- * (A D^2 A') dy = w of the LP given by (gamma, in_lp, mask):
- * d2[nframes x (n+m)], w[nframes x m] in; dy[nframes x m] and
- * iters[nframes] out. Runs in the context's precision mode. */
+/* One Newton solve (Eq. 24) as the decoder does it: PCG (Algorithm 4) with
+ * the context's triangular-set preconditioner (weights d2; lpdec_params.
+ * precond, column-wise for LPDEC_MTS_ADAPTIVE) in the context's precision
+ * mode, and the dense fallback when PCG stalls, for (A D^2 A') dy = w of
+ * the LP given by (gamma, in_lp, mask): d2[nframes x (n+m)], w[nframes x m]
+ * in; dy[nframes x m] and iters[nframes] (PCG iterations) out. */
 int32_t lpdec_pcg_device(lpdec_ctx* ctx, const lpdec_code* code, int32_t nframes,
                          const double* d_gamma, const uint8_t* d_in_lp,
                          const uint32_t* d_mask, const double* d_d2,
